@@ -1,0 +1,237 @@
+"""Seeded synthetic workloads shaped like the paper's data sets.
+
+The paper joins taxi pick-ups against street polylines (P2P, Sec. IV.A) and
+species occurrences against ecoregion polygons (PIP, Sec. IV.A).  Those data
+sets are not available here, so these generators produce inputs with the same
+structure: clustered point clouds, short random-walk polylines, and disjoint
+polygon tilings with uneven vertex counts.
+
+This module holds no arithmetic of the join itself (no cell ids, no
+crossing tests, no distances).  Both the CUDA path and the CPU oracle consume
+its arrays; neither imports the other.
+
+Layer formats (all numpy, C-contiguous):
+  points         float64 [N, 2]          (x, y) in metres
+  polygon layer  verts float64 [V, 2], ring_off int64 [R + 1],
+                 poly_ring_off int64 [P + 1]; ring r owns vertices
+                 ring_off[r] .. ring_off[r + 1] - 1 (implicitly closed),
+                 polygon p owns rings poly_ring_off[p] .. poly_ring_off[p + 1] - 1
+  polyline layer verts float64 [V, 2], line_off int64 [L + 1]
+  grid           dict(x0, y0, x1, y1, nx, ny)
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+EXTENT = 100_000.0          # metres; every workload lives on [0, EXTENT]^2
+SEED_BASE = 20140304        # seed of workload k is SEED_BASE + k
+
+
+def grid(nx: int, ny: int | None = None, extent: float = EXTENT) -> dict:
+    ny = nx if ny is None else ny
+    return dict(x0=0.0, y0=0.0, x1=float(extent), y1=float(extent), nx=int(nx), ny=int(ny))
+
+
+# --------------------------------------------------------------------------- points
+
+def points_uniform(n: int, rng: np.random.Generator, extent: float = EXTENT) -> np.ndarray:
+    """Uniform points on [0, extent)^2."""
+    return np.ascontiguousarray(rng.uniform(0.0, extent, size=(n, 2)))
+
+
+def points_mixture(n: int, rng: np.random.Generator, n_centres: int = 64,
+                   sigma_frac: float = 0.02, uniform_frac: float = 0.2,
+                   extent: float = EXTENT) -> np.ndarray:
+    """Clustered GPS-like points: a Gaussian mixture plus a uniform background.
+
+    (1 - uniform_frac) of the points come from n_centres isotropic Gaussians
+    (centres uniform on the extent, sigma = sigma_frac * extent); samples that
+    fall outside [0, extent)^2 are redrawn.  The rest are uniform.
+    """
+    sigma = sigma_frac * extent
+    centres = rng.uniform(0.0, extent, size=(n_centres, 2))
+    n_mix = int(round(n * (1.0 - uniform_frac)))
+    out = np.empty((n, 2), dtype=np.float64)
+    which = rng.integers(0, n_centres, size=n_mix)
+    pts = centres[which] + rng.normal(0.0, sigma, size=(n_mix, 2))
+    bad = np.flatnonzero((pts < 0.0).any(1) | (pts >= extent).any(1))
+    while bad.size:
+        pts[bad] = centres[which[bad]] + rng.normal(0.0, sigma, size=(bad.size, 2))
+        sub = pts[bad]
+        bad = bad[(sub < 0.0).any(1) | (sub >= extent).any(1)]
+    out[:n_mix] = pts
+    out[n_mix:] = rng.uniform(0.0, extent, size=(n - n_mix, 2))
+    perm = rng.permutation(n)
+    return np.ascontiguousarray(out[perm])
+
+
+# --------------------------------------------------------------------------- polygons
+
+@dataclass
+class PolygonLayer:
+    verts: np.ndarray
+    ring_off: np.ndarray
+    poly_ring_off: np.ndarray
+
+    @property
+    def n_polygons(self) -> int:
+        return len(self.poly_ring_off) - 1
+
+    @property
+    def n_rings(self) -> int:
+        return len(self.ring_off) - 1
+
+    def ring_sizes(self) -> np.ndarray:
+        return np.diff(self.ring_off)
+
+    def polygon_sizes(self) -> np.ndarray:
+        return np.diff(self.ring_off[self.poly_ring_off])
+
+
+@dataclass
+class PolylineLayer:
+    verts: np.ndarray
+    line_off: np.ndarray
+
+    @property
+    def n_lines(self) -> int:
+        return len(self.line_off) - 1
+
+    def line_sizes(self) -> np.ndarray:
+        return np.diff(self.line_off)
+
+
+def _sorted_angles(n: int, rng: np.random.Generator) -> np.ndarray:
+    """n distinct sorted angles in [0, 2pi) whose largest circular gap is < pi.
+
+    The gap rule keeps the centre inside the kernel of the polygon, so the
+    polygon built from these angles is star-shaped and therefore simple.
+    """
+    while True:
+        a = np.sort(rng.uniform(0.0, 2.0 * math.pi, size=n))
+        gaps = np.diff(np.concatenate([a, [a[0] + 2.0 * math.pi]]))
+        if np.all(gaps > 0.0) and gaps.max() < math.pi:
+            return a
+
+
+def star_polygons(rng: np.random.Generator, n_side: int = 32, extent: float = EXTENT,
+                  nmin: int = 8, nmax: int = 64, jitter: float = 0.05,
+                  rmin: float = 0.25, rmax: float = 0.45) -> PolygonLayer:
+    """One star-shaped polygon per cell of an n_side x n_side lattice.
+
+    Polygon id = row * n_side + col (row along y).  Centre = lattice-cell centre
+    jittered by U(-jitter, jitter) * s per axis; n ~ U{nmin..nmax} vertices at
+    sorted uniform angles with radius U(rmin, rmax) * s.  With jitter + rmax <=
+    0.5 every polygon stays inside its own lattice cell, so the layer is
+    disjoint.
+    """
+    s = extent / n_side
+    verts, sizes = [], []
+    for row in range(n_side):
+        for col in range(n_side):
+            cx = (col + 0.5) * s + rng.uniform(-jitter, jitter) * s
+            cy = (row + 0.5) * s + rng.uniform(-jitter, jitter) * s
+            n = int(rng.integers(nmin, nmax + 1))
+            ang = _sorted_angles(n, rng)
+            r = rng.uniform(rmin, rmax, size=n) * s
+            verts.append(np.stack([cx + r * np.cos(ang), cy + r * np.sin(ang)], 1))
+            sizes.append(n)
+    v = np.ascontiguousarray(np.concatenate(verts))
+    ring_off = np.zeros(len(sizes) + 1, np.int64)
+    ring_off[1:] = np.cumsum(sizes)
+    return PolygonLayer(v, ring_off, np.arange(len(sizes) + 1, dtype=np.int64))
+
+
+# --------------------------------------------------------------------------- polylines
+
+def _segmented_cumsum(vals: np.ndarray, starts: np.ndarray) -> np.ndarray:
+    cs = np.cumsum(vals)
+    base = cs[starts] - vals[starts]
+    lens = np.diff(np.append(starts, len(vals)))
+    return cs - np.repeat(base, lens)
+
+
+def random_walks(rng: np.random.Generator, sizes: np.ndarray, extent: float = EXTENT,
+                 step_mean: float = 50.0, step_sd: float = 15.0, step_min: float = 1.0,
+                 turn_sd: float = math.pi / 6.0) -> PolylineLayer:
+    """Street-like polylines as seeded random walks.
+
+    Polyline l has sizes[l] vertices: start uniform on the extent, initial
+    heading U[0, 2pi), each later step turns by N(0, turn_sd) and has length
+    N(step_mean, step_sd) clipped below at step_min.  Vertices are clamped to
+    the closed extent; clamping can create zero-length segments, which are kept.
+    """
+    sizes = np.asarray(sizes, dtype=np.int64)
+    L = len(sizes)
+    off = np.zeros(L + 1, np.int64)
+    off[1:] = np.cumsum(sizes)
+    V = int(off[-1])
+    starts = off[:-1]
+    first = np.zeros(V, bool)
+    first[starts] = True
+    turn = rng.normal(0.0, turn_sd, size=V)
+    turn[first] = 0.0
+    turn[starts[sizes > 1] + 1] = 0.0  # the first step uses the initial heading
+    head0 = rng.uniform(0.0, 2.0 * math.pi, size=L)
+    heading = np.repeat(head0, sizes) + _segmented_cumsum(turn, starts)
+    step = np.maximum(rng.normal(step_mean, step_sd, size=V), step_min)
+    step[first] = 0.0
+    dx = step * np.cos(heading)
+    dy = step * np.sin(heading)
+    start = rng.uniform(0.0, extent, size=(L, 2))
+    x = np.repeat(start[:, 0], sizes) + _segmented_cumsum(dx, starts)
+    y = np.repeat(start[:, 1], sizes) + _segmented_cumsum(dy, starts)
+    v = np.stack([np.clip(x, 0.0, extent), np.clip(y, 0.0, extent)], 1)
+    return PolylineLayer(np.ascontiguousarray(v), off)
+
+
+# --------------------------------------------------------------------------- named workloads
+
+@dataclass
+class Workload:
+    name: str
+    kind: str                       # "pip" or "p2p"
+    points: np.ndarray
+    grid: dict
+    polygons: PolygonLayer | None = None
+    polylines: PolylineLayer | None = None
+    D: float = 0.0
+    meta: dict = field(default_factory=dict)
+
+
+def pip_stars(n_points: int = 1_000_000, seed: int = SEED_BASE + 1, n_side: int = 32,
+              grid_n: int = 256) -> Workload:
+    """PIP, plain FP64 method: uniform points against a jittered lattice of
+    1,024 star polygons (8-64 vertices), filter grid 256 x 256."""
+    rng = np.random.default_rng(seed)
+    layer = star_polygons(rng, n_side=n_side)
+    pts = points_uniform(n_points, rng)
+    return Workload("pip_1M_stars1024_grid256", "pip", pts, grid(grid_n), polygons=layer)
+
+
+def p2p_walks(n_points: int = 10_000_000, n_lines: int = 100_000, seed: int = SEED_BASE + 2,
+              D: float = 100.0, grid_n: int = 1024) -> Workload:
+    """P2P, plain FP64 method: mixture points against random-walk polylines with
+    2-40 vertices, window D = 100 m, filter grid 1024 x 1024."""
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(2, 41, size=n_lines)
+    layer = random_walks(rng, sizes)
+    pts = points_mixture(n_points, rng)
+    return Workload("p2p_10M_walks100k_D100_grid1024", "p2p", pts, grid(grid_n),
+                    polylines=layer, D=float(D))
+
+
+def p2p_walks_lognormal(n_points: int = 170_000_000, n_lines: int = 150_000,
+                        seed: int = SEED_BASE + 4, D: float = 100.0,
+                        grid_n: int = 1024) -> Workload:
+    """P2P at scale: mixture points against random walks whose vertex counts are
+    clamp(round(lognormal(ln 8, 0.8)), 2, 200)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.clip(np.round(rng.lognormal(math.log(8.0), 0.8, size=n_lines)), 2, 200).astype(np.int64)
+    layer = random_walks(rng, sizes)
+    pts = points_mixture(n_points, rng)
+    return Workload(f"p2p_{n_points}_walks{n_lines}_D{int(D)}_grid{grid_n}", "p2p", pts,
+                    grid(grid_n), polylines=layer, D=float(D))
