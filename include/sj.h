@@ -1,0 +1,205 @@
+/*
+ * sj.h -- C ABI of the GB300 grid-filtered spatial join (libsj.so).
+ *
+ * The library implements the data-parallel spatial join of Zhang & You,
+ * "Large-Scale Geospatial Processing on Multi-Core and Many-Core Processors"
+ * (arXiv 1403.0802):
+ *   - a uniform-grid filter (Sec. III.A, Fig. 1): points are bucketed by grid
+ *     cell, and polygon / polyline minimum bounding boxes (MBBs) are rasterised
+ *     to the same grid, giving per-cell candidate lists;
+ *   - PIP refinement (Sec. III.C, Fig. 3): ray-crossing point-in-polygon test
+ *     over every ring of a candidate polygon (holes allowed);
+ *   - P2P refinement (Sec. III.B, Fig. 2): nearest polyline within a window
+ *     R (called D here), by the minimum point-to-segment distance.
+ *
+ * Conventions shared by every entry point:
+ *   - Coordinates are FP64 metres, points and vertices are interleaved
+ *     (x, y) pairs, i.e. [n, 2] row-major arrays; point / vertex arrays must be
+ *     16-byte aligned.
+ *   - "dev" pointers are CUDA device pointers, "host" pointers are host memory.
+ *     The caller owns every buffer it passes in.  The library owns sj_layer
+ *     objects and the scratch memory of each call (stream-ordered allocations
+ *     on the caller's stream).
+ *   - stream is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream.  Joins are asynchronous on it; argument errors are returned
+ *     synchronously and leave the outputs untouched.
+ *   - Ids are 0-based int32.  The join domain is the half-open grid box
+ *     [x0, x1) x [y0, y1): points outside it get id -1 (and distance +inf).
+ *   - Readings of the paper used here (the paper is silent on them):
+ *       cell of (x, y): ix = floor((x - x0) / cw), cw = (x1 - x0) / nx, in FP64;
+ *       an edge (a, b) straddles p iff (a.y > p.y) != (b.y > p.y); with lo the
+ *       end at or below p.y and hi the other, it counts iff
+ *       (hi.x - lo.x) * (p.y - lo.y) - (hi.y - lo.y) * (p.x - lo.x) > 0
+ *       (FP64, each operation rounded, no fused multiply-add); inside iff the
+ *       count over all rings is odd; a point inside several polygons gets the
+ *       smallest id; the P2P window is inclusive (d <= D) and equal distances
+ *       go to the smaller id.
+ *   - Every function returns an sj_status; on failure sj_last_error() gives a
+ *     message (thread-local, valid until the next call on that thread).
+ */
+#ifndef SJ_H
+#define SJ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Uniform grid over [x0, x1) x [y0, y1) with nx * ny cells (Sec. III.A).
+ * Requires x1 > x0, y1 > y0, nx, ny >= 1 and nx * ny < 2^31 - 1. */
+typedef struct {
+    double x0, y0, x1, y1;
+    int32_t nx, ny;
+} sj_grid;
+
+typedef enum {
+    SJ_OK = 0,
+    SJ_ERR_INVALID = -1,    /* bad argument, bad layer topology, NaN / inf vertex  */
+    SJ_ERR_OOM = -2,        /* device allocation failed                            */
+    SJ_ERR_GRID_COVER = -3, /* an MBB is not inside the closed grid box            */
+    SJ_ERR_CUDA = -4,       /* a CUDA call failed (message in sj_last_error)       */
+    SJ_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                       */
+    SJ_ERR_BUSY = -6        /* resource in use                                     */
+} sj_status;
+
+/* Refinement arithmetic. */
+enum {
+    SJ_FP64 = 0,  /* plain FP64 refinement                                        */
+    SJ_FP32X = 1  /* cell-relative FP32 with FP64 fallback: PIP ids are identical
+                     to the FP64 rule; P2P ids are exact (ties aside) and the
+                     distance error is bounded per point                           */
+};
+
+/* Launch form. */
+enum {
+    SJ_PER_REQUEST = 0, /* one pass of kernels per call                           */
+    SJ_PERSISTENT = 1   /* persistent, cost-balanced refinement (same results)    */
+};
+
+/* Join options; a zeroed struct (or NULL) selects the defaults. */
+typedef struct {
+    int32_t form;            /* SJ_FP64 (default) or SJ_FP32X                       */
+    int32_t launch;          /* SJ_PER_REQUEST (default) or SJ_PERSISTENT           */
+    int32_t block;           /* threads per refinement block (multiple of 32), 0 = default */
+    int32_t pts_per_item;    /* points per work item, 1..128, 0 = default (64)     */
+    int32_t edges_per_chunk; /* reserved, 0                                         */
+    int32_t flags;           /* SJ_FLAG_* bits                                      */
+} sj_opts;
+
+/* opts.flags: record CUDA events on the call's stream around the refinement
+ * kernels; their summed elapsed time is reported by sj_layer_get_stats. */
+#define SJ_FLAG_TIME_REFINE 1
+
+typedef struct sj_layer sj_layer;
+
+typedef struct {
+    int32_t kind;         /* 0 = polygon layer (PIP), 1 = polyline layer (P2P)  */
+    int32_t n_objects;    /* polygons or polylines                              */
+    int64_t n_vertices;
+    int64_t n_rings;      /* polygon layers; = n_objects for polyline layers    */
+    int64_t n_cells;      /* G = nx * ny                                        */
+    int64_t n_candidates; /* M = number of (cell, object) candidate pairs       */
+    double D;             /* P2P window (0 for polygon layers)                  */
+} sj_layer_info;
+
+/* Counters accumulated by the joins run on a layer since the last reset. */
+typedef struct {
+    int64_t joins;
+    int64_t points;        /* points submitted                                  */
+    int64_t items;         /* (cell, point-chunk) work items                    */
+    int64_t pairs;         /* (point, candidate object) pairs refined            */
+    int64_t edge_tests;    /* PIP: point x edge tests; P2P: point x segment tests */
+    int64_t fallbacks;     /* SJ_FP32X: PIP edges / P2P points redone in FP64   */
+    int64_t hits;          /* points given an id                                 */
+    int64_t refine_launches; /* refinement launches timed (SJ_FLAG_TIME_REFINE)  */
+    double refine_ms;        /* their summed device time, milliseconds           */
+} sj_run_stats;
+
+/* Build a resident polygon layer and its candidate lists (Sec. III.A: MBB of
+ * each polygon rasterised to the grid; Sec. III.C: no expansion for PIP).
+ *   verts          dev  [V, 2] f64 vertices; ring r owns ring_off[r] .. ring_off[r+1]-1,
+ *                       implicitly closed (a repeated closing vertex is harmless)
+ *   ring_off       dev  [R + 1] int64, ring_off[0] = 0, ring_off[R] = V, rings >= 3 vertices
+ *   poly_ring_off  dev  [P + 1] int64, polygon p owns rings poly_ring_off[p] .. [p+1]-1
+ *                       (outer ring and holes alike: even-odd rule), >= 1 ring each
+ *   g              host grid; every polygon MBB must lie in the closed grid box
+ * The input arrays are copied; the caller may free them after return.  The
+ * call synchronises `stream` (it reads validation results back).
+ * Errors: SJ_ERR_INVALID (topology, NaN/inf, V >= 2^31), SJ_ERR_GRID_COVER,
+ * SJ_ERR_OOM, SJ_ERR_CUDA. */
+sj_status sj_pip_layer_create(const double *verts, int64_t V, const int64_t *ring_off, int64_t R,
+                              const int64_t *poly_ring_off, int32_t P, const sj_grid *g, void *stream,
+                              sj_layer **out);
+
+/* Build a resident polyline layer for window D (Sec. III.A: expanded MBB
+ * (x1 - D, y1 - D, x2 + D, y2 + D), rounded outward by one ulp).
+ *   verts     dev [V, 2] f64; polyline l owns line_off[l] .. line_off[l+1]-1 (>= 1 vertex;
+ *                 a one-vertex polyline is a point)
+ *   line_off  dev [L + 1] int64
+ *   D         window, finite and >= 0
+ * Same ownership, synchronisation and errors as sj_pip_layer_create. */
+sj_status sj_p2p_layer_create(const double *verts, int64_t V, const int64_t *line_off, int32_t L, double D,
+                              const sj_grid *g, void *stream, sj_layer **out);
+
+/* Free a layer (synchronises the device before freeing).  NULL is a no-op. */
+sj_status sj_layer_destroy(sj_layer *layer);
+
+sj_status sj_layer_get_info(const sj_layer *layer, sj_layer_info *out);
+
+/* Copy the layer's candidate lists to host memory (Fig. 1, VPP relation in
+ * CSR form): cand_start [G + 1] int32, cand_ids [M] int32 sorted by id within
+ * each cell.  Synchronous. */
+sj_status sj_layer_get_candidates(const sj_layer *layer, int32_t *cand_start, int32_t *cand_ids);
+
+/* Point-in-polygon join (Sec. III.C): out_id[i] = smallest polygon id whose
+ * even-odd ray-crossing count for point i is odd, else -1.
+ *   pts     dev [N, 2] f64, 16-byte aligned
+ *   out_id  dev [N] int32
+ *   opts    may be NULL
+ * N < 2^31.  Asynchronous on stream. */
+sj_status sj_pip_join(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, const sj_opts *opts,
+                      void *stream);
+
+/* Point-to-polyline join (Sec. III.B): for each point the polyline with the
+ * smallest distance (ties: smaller id) if that distance is <= D:
+ * out_id[i] = its id, out_d[i] = the distance; else -1 and +inf.
+ *   pts     dev [N, 2] f64; out_id dev [N] int32; out_d dev [N] f64 (may be NULL)
+ * SJ_FP64 distances agree with the FP64 two-case formula to 1e-12 * max(d, 1 m);
+ * SJ_FP32X distances are within a per-point bound (about 64 * 2^-24 times the
+ * largest cell-relative coordinate involved).  Asynchronous on stream. */
+sj_status sj_p2p_join(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                      const sj_opts *opts, void *stream);
+
+/* Same joins from HOST buffers: the library copies the points to the device,
+ * joins, copies the results back, and synchronises `stream` before returning.
+ * pts / out_id / out_d are host pointers (pinned memory gives overlap-free
+ * full-bandwidth copies; pageable memory works too). */
+sj_status sj_pip_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id,
+                           const sj_opts *opts, void *stream);
+sj_status sj_p2p_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                           const sj_opts *opts, void *stream);
+
+/* Point bucketing alone (Sec. III.A, Fig. 1 top-left: sort points by cell id,
+ * VGC/VGI vectors): cell_start [G + 1] int32 dev gets the exclusive prefix sum
+ * of per-cell point counts (cell_start[G] = in-grid points) and perm [N] int32
+ * dev the input index of each sorted slot (order within a cell unspecified;
+ * slots past cell_start[G] are left untouched).  Asynchronous on stream. */
+sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32_t *cell_start, int32_t *perm,
+                           void *stream);
+
+/* Counters of the joins run on `layer` (synchronises the device). */
+sj_status sj_layer_get_stats(const sj_layer *layer, sj_run_stats *out);
+sj_status sj_layer_reset_stats(sj_layer *layer);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sj_last_error(void);
+
+/* Library version string. */
+const char *sj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SJ_H */

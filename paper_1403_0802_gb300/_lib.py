@@ -1,0 +1,88 @@
+"""ctypes loader of the in-tree libsj.so (the C ABI declared in include/sj.h).
+
+The library must have been built (``paper_1403_0802_gb300.build.build()`` or
+``__graft_entry__.build()``); there is no fallback: loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+from .build import SO
+
+_lock = threading.Lock()
+_lib = None
+
+
+class sj_grid(C.Structure):
+    _fields_ = [("x0", C.c_double), ("y0", C.c_double), ("x1", C.c_double), ("y1", C.c_double),
+                ("nx", C.c_int32), ("ny", C.c_int32)]
+
+
+class sj_opts(C.Structure):
+    _fields_ = [("form", C.c_int32), ("launch", C.c_int32), ("block", C.c_int32), ("pts_per_item", C.c_int32),
+                ("edges_per_chunk", C.c_int32), ("flags", C.c_int32)]
+
+
+class sj_layer_info(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n_objects", C.c_int32), ("n_vertices", C.c_int64), ("n_rings", C.c_int64),
+                ("n_cells", C.c_int64), ("n_candidates", C.c_int64), ("D", C.c_double)]
+
+
+class sj_run_stats(C.Structure):
+    _fields_ = [("joins", C.c_int64), ("points", C.c_int64), ("items", C.c_int64), ("pairs", C.c_int64),
+                ("edge_tests", C.c_int64), ("fallbacks", C.c_int64), ("hits", C.c_int64),
+                ("refine_launches", C.c_int64), ("refine_ms", C.c_double)]
+
+
+SJ_OK, SJ_ERR_INVALID, SJ_ERR_OOM, SJ_ERR_GRID_COVER, SJ_ERR_CUDA, SJ_ERR_TIMEOUT, SJ_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
+SJ_FP64, SJ_FP32X = 0, 1
+SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
+SJ_FLAG_TIME_REFINE = 1
+
+# name -> (restype, argtypes); every name here is declared in include/sj.h
+_P, _I32, _I64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_LP = C.POINTER(C.c_void_p)
+SIGNATURES = {
+    "sj_pip_layer_create": (C.c_int, [_P, _I64, _P, _I64, _P, _I32, C.POINTER(sj_grid), _P, _LP]),
+    "sj_p2p_layer_create": (C.c_int, [_P, _I64, _P, _I32, _D, C.POINTER(sj_grid), _P, _LP]),
+    "sj_layer_destroy": (C.c_int, [_P]),
+    "sj_layer_get_info": (C.c_int, [_P, C.POINTER(sj_layer_info)]),
+    "sj_layer_get_candidates": (C.c_int, [_P, _P, _P]),
+    "sj_pip_join": (C.c_int, [_P, _P, _I64, _P, C.POINTER(sj_opts), _P]),
+    "sj_p2p_join": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
+    "sj_pip_join_host": (C.c_int, [_P, _P, _I64, _P, C.POINTER(sj_opts), _P]),
+    "sj_p2p_join_host": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
+    "sj_bucket_points": (C.c_int, [_P, _I64, C.POINTER(sj_grid), _P, _P, _P]),
+    "sj_layer_get_stats": (C.c_int, [_P, C.POINTER(sj_run_stats)]),
+    "sj_layer_reset_stats": (C.c_int, [_P]),
+    "sj_last_error": (C.c_char_p, []),
+    "sj_version": (C.c_char_p, []),
+}
+
+
+class SJError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(SO):
+                raise RuntimeError(f"libsj.so is not built ({SO}); run paper_1403_0802_gb300.build.build()")
+            L = C.CDLL(SO)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def check(status: int, where: str):
+    if status != SJ_OK:
+        raise SJError(status, where, lib().sj_last_error().decode())

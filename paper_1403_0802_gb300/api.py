@@ -1,0 +1,215 @@
+"""Python front end of libsj.so: argument marshalling only.
+
+Every step of the join runs in the library's CUDA kernels; this module turns
+torch tensors (device memory, streams) and numpy arrays into the pointers and
+sizes of the C ABI in include/sj.h.
+
+    layer = pip_layer(verts, ring_off, poly_ring_off, grid)      # resident polygon layer
+    ids = pip_join(layer, pts)                                     # torch int32 [N] on the GPU
+    layer = p2p_layer(verts, line_off, D, grid)                    # resident polyline layer
+    ids, d = p2p_join(layer, pts, form="fp32x")                    # nearest polyline within D
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+FORMS = {"fp64": L.SJ_FP64, "fp32x": L.SJ_FP32X}
+LAUNCHES = {"per_request": L.SJ_PER_REQUEST, "persistent": L.SJ_PERSISTENT}
+
+
+def _grid(g) -> L.sj_grid:
+    return L.sj_grid(float(g["x0"]), float(g["y0"]), float(g["x1"]), float(g["y1"]), int(g["nx"]), int(g["ny"]))
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
+
+
+def _opts(form="fp64", launch="per_request", pts_per_item=0, time_refine=False) -> L.sj_opts:
+    return L.sj_opts(FORMS[form], LAUNCHES[launch], 0, int(pts_per_item), 0,
+                     L.SJ_FLAG_TIME_REFINE if time_refine else 0)
+
+
+def _dev(a, dtype, device="cuda") -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        t = a.to(device=device, dtype=dtype)
+    else:
+        t = torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device=device)
+    return t.contiguous()
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None or t.numel() == 0 else t.data_ptr()
+
+
+class Layer:
+    """A resident polygon (kind 0) or polyline (kind 1) layer with its grid index."""
+
+    def __init__(self, handle: int, grid: dict, kind: int, D: float = 0.0):
+        self._h = C.c_void_p(handle)
+        self.grid = dict(grid)
+        self.kind = kind
+        self.D = D
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise RuntimeError("layer destroyed")
+        return self._h
+
+    def info(self) -> dict:
+        inf = L.sj_layer_info()
+        L.check(L.lib().sj_layer_get_info(self.handle, C.byref(inf)), "sj_layer_get_info")
+        return {f: getattr(inf, f) for f, _ in inf._fields_}
+
+    def candidates(self):
+        """Per-cell candidate lists: (cand_start int32 [G+1], cand_ids int32 [M])."""
+        inf = self.info()
+        start = np.empty(inf["n_cells"] + 1, np.int32)
+        ids = np.empty(max(inf["n_candidates"], 1), np.int32)
+        L.check(L.lib().sj_layer_get_candidates(self.handle, start.ctypes.data, ids.ctypes.data),
+                "sj_layer_get_candidates")
+        return start, ids[:inf["n_candidates"]]
+
+    def stats(self) -> dict:
+        st = L.sj_run_stats()
+        L.check(L.lib().sj_layer_get_stats(self.handle, C.byref(st)), "sj_layer_get_stats")
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def reset_stats(self):
+        L.check(L.lib().sj_layer_reset_stats(self.handle), "sj_layer_reset_stats")
+
+    def close(self):
+        if self._h:
+            L.lib().sj_layer_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def pip_layer(verts, ring_off, poly_ring_off, grid: dict, stream=None) -> Layer:
+    v = _dev(verts, torch.float64).reshape(-1, 2)
+    ro = _dev(ring_off, torch.int64)
+    pro = _dev(poly_ring_off, torch.int64)
+    h = C.c_void_p()
+    g = _grid(grid)
+    L.check(L.lib().sj_pip_layer_create(_ptr(v), v.shape[0], ro.data_ptr(), ro.numel() - 1, pro.data_ptr(),
+                                        pro.numel() - 1, C.byref(g), _stream(stream), C.byref(h)),
+            "sj_pip_layer_create")
+    return Layer(h.value, grid, 0)
+
+
+def p2p_layer(verts, line_off, D: float, grid: dict, stream=None) -> Layer:
+    v = _dev(verts, torch.float64).reshape(-1, 2)
+    lo = _dev(line_off, torch.int64)
+    h = C.c_void_p()
+    g = _grid(grid)
+    L.check(L.lib().sj_p2p_layer_create(_ptr(v), v.shape[0], lo.data_ptr(), lo.numel() - 1, float(D), C.byref(g),
+                                        _stream(stream), C.byref(h)), "sj_p2p_layer_create")
+    return Layer(h.value, grid, 1, float(D))
+
+
+def _points(pts) -> torch.Tensor:
+    p = pts if isinstance(pts, torch.Tensor) and pts.is_cuda else _dev(pts, torch.float64)
+    if p.dtype != torch.float64 or p.dim() != 2 or p.shape[1] != 2:
+        raise ValueError("points must be a float64 [N, 2] tensor")
+    return p.contiguous()
+
+
+def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp64", launch: str = "per_request",
+             pts_per_item: int = 0, stream=None, time_refine: bool = False) -> torch.Tensor:
+    """Polygon id (or -1) per point, int32 on the points' device (Sec. III.C)."""
+    p = _points(pts)
+    out = torch.empty(p.shape[0], dtype=torch.int32, device=p.device) if out is None else out
+    o = _opts(form, launch, pts_per_item, time_refine)
+    L.check(L.lib().sj_pip_join(layer.handle, _ptr(p), p.shape[0], _ptr(out), C.byref(o), _stream(stream)),
+            "sj_pip_join")
+    return out
+
+
+def p2p_join(layer: Layer, pts, out_id: torch.Tensor | None = None, out_d: torch.Tensor | None = None,
+             form: str = "fp64", launch: str = "per_request", pts_per_item: int = 0, stream=None,
+             time_refine: bool = False):
+    """(nearest polyline id or -1, distance or +inf) per point (Sec. III.B)."""
+    p = _points(pts)
+    n = p.shape[0]
+    out_id = torch.empty(n, dtype=torch.int32, device=p.device) if out_id is None else out_id
+    out_d = torch.empty(n, dtype=torch.float64, device=p.device) if out_d is None else out_d
+    o = _opts(form, launch, pts_per_item, time_refine)
+    L.check(L.lib().sj_p2p_join(layer.handle, _ptr(p), n, _ptr(out_id), _ptr(out_d), C.byref(o), _stream(stream)),
+            "sj_p2p_join")
+    return out_id, out_d
+
+
+def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, form: str = "fp64",
+                  stream=None) -> np.ndarray:
+    """Same as pip_join from host memory (copies in and out; synchronous)."""
+    p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
+    n = p.shape[0]
+    out = np.empty(n, np.int32) if out is None else out
+    o = _opts(form)
+    pp = p.data_ptr() if isinstance(p, torch.Tensor) else p.ctypes.data
+    op = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
+    L.check(L.lib().sj_pip_join_host(layer.handle, pp, n, op, C.byref(o), _stream(stream)), "sj_pip_join_host")
+    return out
+
+
+def p2p_join_host(layer: Layer, pts, out_id=None, out_d=None, form: str = "fp64", stream=None):
+    p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
+    n = p.shape[0]
+    out_id = np.empty(n, np.int32) if out_id is None else out_id
+    out_d = np.empty(n, np.float64) if out_d is None else out_d
+    o = _opts(form)
+    ptr = lambda a: a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+    L.check(L.lib().sj_p2p_join_host(layer.handle, ptr(p), n, ptr(out_id), ptr(out_d), C.byref(o), _stream(stream)),
+            "sj_p2p_join_host")
+    return out_id, out_d
+
+
+def bucket_points(pts, grid: dict, stream=None):
+    """Cell bucketing alone (Sec. III.A): (cell_start int32 [G+1], perm int32 [N])."""
+    p = _points(pts)
+    G = int(grid["nx"]) * int(grid["ny"])
+    cs = torch.empty(G + 1, dtype=torch.int32, device=p.device)
+    perm = torch.full((p.shape[0],), -1, dtype=torch.int32, device=p.device)
+    g = _grid(grid)
+    L.check(L.lib().sj_bucket_points(_ptr(p), p.shape[0], C.byref(g), cs.data_ptr(), _ptr(perm), _stream(stream)),
+            "sj_bucket_points")
+    return cs, perm
+
+
+def pip_join_once(points, verts, ring_off, poly_ring_off, grid: dict, form: str = "fp64") -> torch.Tensor:
+    """pip_join(points, polygons, grid): build the layer, join, free it."""
+    with pip_layer(verts, ring_off, poly_ring_off, grid) as layer:
+        out = pip_join(layer, points, form=form)
+        torch.cuda.current_stream().synchronize()
+        return out
+
+
+def p2p_join_once(points, verts, line_off, D: float, grid: dict, form: str = "fp64"):
+    """p2p_join(points, polylines, D, grid): build the layer, join, free it."""
+    with p2p_layer(verts, line_off, D, grid) as layer:
+        res = p2p_join(layer, points, form=form)
+        torch.cuda.current_stream().synchronize()
+        return res
+
+
+def version() -> str:
+    return L.lib().sj_version().decode()

@@ -1,0 +1,665 @@
+// sj_api.cu -- C ABI of libsj.so (declared in include/sj.h): argument checks,
+// layer construction (validation, MBBs, candidate lists) and the join
+// pipelines (bucketing -> work items -> refinement), all stream-ordered.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <atomic>
+#include <cmath>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "sj.h"
+#include "sj_internal.cuh"
+
+namespace sj {
+cudaError_t launch_check_offsets(const int64_t *off, int64_t n, int64_t min_size, int64_t first, int64_t last, int *out,
+                                 int *bad, cudaStream_t s);
+cudaError_t launch_check_finite(const double2 *v, int n, int *bad, cudaStream_t s);
+cudaError_t launch_pip_topology(const int *ring_off, int R, const int *poly_ring_off, int P, int *poly_voff, int *nxt,
+                                cudaStream_t s);
+cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s);
+cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
+                             float *inv32, cudaStream_t s);
+cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s);
+cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *total, cudaStream_t s);
+cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s);
+int pip_blocks_per_sm(int form);
+int p2p_blocks_per_sm(int form);
+}  // namespace sj
+
+using namespace sj;
+
+struct sj_layer {
+    int kind = 0;
+    int device = 0;
+    sj_grid grid{};
+    GridDev g{};
+    int nobj = 0;
+    int V = 0;
+    int64_t R = 0;
+    double D = 0.0;
+    int64_t M = 0;
+    float eps_abs = 0.0f;
+    double2 *verts = nullptr;
+    float4 *vsplit = nullptr;
+    int *obj_voff = nullptr;
+    int *nxt = nullptr;
+    int *ring_off = nullptr;
+    int *poly_ring_off = nullptr;
+    double2 *seg_e64 = nullptr;
+    double *seg_inv64 = nullptr;
+    float2 *seg_e32 = nullptr;
+    float *seg_inv32 = nullptr;
+    Box *mbb = nullptr;
+    int *cand_start = nullptr;
+    int *cand_ids = nullptr;
+    unsigned long long *stats = nullptr;
+    mutable std::atomic<long long> joins{0};
+    mutable std::atomic<long long> points{0};
+    // SJ_FLAG_TIME_REFINE: event pairs recorded around refinement launches,
+    // resolved (and destroyed) by sj_layer_get_stats.
+    mutable std::mutex ev_mu;
+    mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    mutable double refine_ms = 0.0;
+    mutable long long refine_launches = 0;
+};
+
+// ------------------------------------------------------------------ errors
+
+static thread_local std::string g_err;
+
+static sj_status fail(sj_status st, const std::string &msg) {
+    g_err = msg;
+    return st;
+}
+
+static sj_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(e == cudaErrorMemoryAllocation ? SJ_ERR_OOM : SJ_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(x)                                    \
+    do {                                               \
+        cudaError_t e_ = (x);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
+    } while (0)
+
+// ------------------------------------------------------------------ device info
+
+struct DevInfo {
+    int sms = 0;
+    int pip_bps[2] = {0, 0};
+    int p2p_bps[2] = {0, 0};
+    bool init = false;
+};
+static DevInfo g_dev[64];
+static std::mutex g_dev_mu;
+
+static sj_status device_info(int dev, DevInfo **out) {
+    if (dev < 0 || dev >= 64) return fail(SJ_ERR_INVALID, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DevInfo &d = g_dev[dev];
+    if (!d.init) {
+        CUDA_TRY(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+        for (int f = 0; f < 2; ++f) {
+            d.pip_bps[f] = pip_blocks_per_sm(f);
+            d.p2p_bps[f] = p2p_blocks_per_sm(f);
+        }
+        // keep freed stream-ordered scratch in the pool for the next call
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        d.init = true;
+    }
+    *out = &d;
+    return SJ_OK;
+}
+
+static bool grid_ok(const sj_grid *g) {
+    if (!g) return false;
+    if (!(g->nx >= 1 && g->ny >= 1)) return false;
+    if ((int64_t)g->nx * (int64_t)g->ny > 2147483646LL) return false;
+    if (!(std::isfinite(g->x0) && std::isfinite(g->x1) && std::isfinite(g->y0) && std::isfinite(g->y1))) return false;
+    return g->x1 > g->x0 && g->y1 > g->y0;
+}
+
+static GridDev make_grid(const sj_grid *g) {
+    GridDev d;
+    d.x0 = g->x0; d.y0 = g->y0; d.x1 = g->x1; d.y1 = g->y1;
+    d.nx = g->nx; d.ny = g->ny;
+    d.G = g->nx * g->ny;
+    volatile double cw = (g->x1 - g->x0) / (double)g->nx;   // one IEEE division each
+    volatile double ch = (g->y1 - g->y0) / (double)g->ny;
+    d.cw = cw; d.ch = ch;
+    return d;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Stream-ordered scratch carved from one allocation.
+struct Scratch {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+template <class F>
+static size_t measure(F f) {
+    Scratch s;
+    f(s);
+    return s.off + 256;
+}
+
+// ------------------------------------------------------------------ layers
+
+// Sum and destroy the pending timing events (the device must be idle).
+static void resolve_events(const sj_layer *L) {
+    std::lock_guard<std::mutex> lk(L->ev_mu);
+    for (auto &p : L->ev_pending) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) {
+            L->refine_ms += ms;
+            L->refine_launches += 1;
+        }
+        cudaEventDestroy(p.first);
+        cudaEventDestroy(p.second);
+    }
+    L->ev_pending.clear();
+}
+
+static void layer_free(sj_layer *L) {
+    resolve_events(L);
+    void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
+                    L->seg_inv64, L->seg_e32, L->seg_inv32, L->mbb, L->cand_start, L->cand_ids, L->stats};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    delete L;
+}
+
+struct LayerGuard {
+    sj_layer *L;
+    ~LayerGuard() {
+        if (L) layer_free(L);
+    }
+};
+
+template <class T>
+static cudaError_t dalloc(T **p, size_t n) {
+    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+}
+
+static sj_status read_flag(int *dflag, cudaStream_t s, int *out) {
+    CUDA_TRY(cudaMemcpyAsync(out, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SJ_OK;
+}
+
+// Shared tail of both layer builders: MBB, cover check, rasterisation, CSR.
+static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
+    LayerBuildArgs a{};
+    a.g = L->g;
+    a.kind = L->kind;
+    a.D = L->D;
+    a.nobj = L->nobj;
+    a.V = L->V;
+    a.verts = L->verts;
+    a.obj_voff = L->obj_voff;
+    a.bad = dbad;
+    CUDA_TRY(dalloc(&L->mbb, (size_t)L->nobj));
+    CUDA_TRY(dalloc(&L->cand_start, (size_t)L->g.G + 1));
+    a.mbb = L->mbb;
+    a.cand_start = L->cand_start;
+
+    int *cell_cnt = nullptr, *cursor = nullptr, *obj_cells = nullptr, *totals = nullptr;
+    int2 *block_sums = nullptr, *pairs = nullptr;
+    unsigned long long *total = nullptr;
+    size_t nbs = (size_t)((std::max(L->g.G, L->nobj) + 4095) / 4096) + 2;
+    struct Tmp {
+        void *p[7] = {};
+        ~Tmp() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } tmp;
+    CUDA_TRY(dalloc(&cell_cnt, (size_t)L->g.G + 1)); tmp.p[0] = cell_cnt;
+    CUDA_TRY(dalloc(&cursor, (size_t)L->g.G)); tmp.p[1] = cursor;
+    CUDA_TRY(dalloc(&obj_cells, (size_t)L->nobj + 1)); tmp.p[2] = obj_cells;
+    CUDA_TRY(dalloc(&block_sums, nbs)); tmp.p[3] = block_sums;
+    CUDA_TRY(dalloc(&totals, 4)); tmp.p[4] = totals;
+    CUDA_TRY(dalloc(&total, 1)); tmp.p[5] = total;
+    CUDA_TRY(cudaMemsetAsync(cell_cnt, 0, sizeof(int) * ((size_t)L->g.G + 1), s));
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)L->g.G, s));
+    CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(unsigned long long), s));
+    a.cell_cnt = cell_cnt;
+    a.cursor = cursor;
+    a.obj_cells = obj_cells;
+    a.block_sums = block_sums;
+    a.totals = totals;
+
+    if (L->nobj > 0) {
+        CUDA_TRY(launch_mbb(a, s));
+        int bad = 0;
+        sj_status st = read_flag(dbad, s, &bad);
+        if (st != SJ_OK) return st;
+        if (bad & 2) return fail(SJ_ERR_GRID_COVER, "an object's MBB is not inside the closed grid box");
+        CUDA_TRY(launch_raster_count(a, total, s));
+    }
+    unsigned long long M = 0;
+    CUDA_TRY(cudaMemcpyAsync(&M, total, sizeof(M), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (M > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (cell, object) candidate pairs");
+    L->M = (int64_t)M;
+    CUDA_TRY(dalloc(&L->cand_ids, (size_t)M));
+    if (L->nobj > 0) {
+        CUDA_TRY(dalloc(&pairs, (size_t)M)); tmp.p[6] = pairs;
+        CUDA_TRY(launch_raster_emit(a, pairs, (int)M, L->cand_ids, s));
+    } else {
+        CUDA_TRY(cudaMemsetAsync(L->cand_start, 0, sizeof(int) * ((size_t)L->g.G + 1), s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    // eps_abs bounds 2 |lo part| + rounding of the hi/lo split for any vertex
+    // inside the grid box: 2.0003 u^2 max|coordinate|.
+    double xm = std::max(std::max(std::fabs(L->grid.x0), std::fabs(L->grid.x1)),
+                         std::max(std::fabs(L->grid.y0), std::fabs(L->grid.y1)));
+    double u = 5.9604644775390625e-08;
+    L->eps_abs = (float)(2.0003 * u * u * xm * (1.0 + 1e-6)) + 1e-30f;
+    return SJ_OK;
+}
+
+static sj_status layer_common_checks(const double *verts, int64_t V, const sj_grid *g, void *stream,
+                                     sj_layer **out, DevInfo **di) {
+    if (!out) return fail(SJ_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!grid_ok(g)) return fail(SJ_ERR_INVALID, "invalid grid");
+    if (V < 0 || V > 2147483647LL) return fail(SJ_ERR_INVALID, "vertex count out of range");
+    if (V > 0 && (!verts || !aligned16(verts))) return fail(SJ_ERR_INVALID, "verts NULL or not 16-byte aligned");
+    (void)stream;
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    return device_info(dev, di);
+}
+
+extern "C" sj_status sj_pip_layer_create(const double *verts, int64_t V, const int64_t *ring_off, int64_t R,
+                                         const int64_t *poly_ring_off, int32_t P, const sj_grid *g, void *stream,
+                                         sj_layer **out) {
+    DevInfo *di;
+    sj_status st = layer_common_checks(verts, V, g, stream, out, &di);
+    if (st != SJ_OK) return st;
+    if (P < 0 || R < 0 || R > 2147483646LL) return fail(SJ_ERR_INVALID, "ring or polygon count out of range");
+    if (!ring_off || !poly_ring_off) return fail(SJ_ERR_INVALID, "offset array is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    LayerGuard guard{new sj_layer()};
+    sj_layer *L = guard.L;
+    L->kind = KIND_PIP;
+    CUDA_TRY(cudaGetDevice(&L->device));
+    L->grid = *g;
+    L->g = make_grid(g);
+    L->nobj = P;
+    L->V = (int)V;
+    L->R = R;
+    int *dbad = nullptr;
+    CUDA_TRY(dalloc(&dbad, 1));
+    struct F { int *p; ~F() { cudaFree(p); } } fbad{dbad};
+    CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), s));
+    CUDA_TRY(dalloc(&L->ring_off, (size_t)R + 1));
+    CUDA_TRY(dalloc(&L->poly_ring_off, (size_t)P + 1));
+    CUDA_TRY(launch_check_offsets(ring_off, R, 3, 0, V, L->ring_off, dbad, s));
+    CUDA_TRY(launch_check_offsets(poly_ring_off, P, 1, 0, R, L->poly_ring_off, dbad, s));
+    CUDA_TRY(dalloc(&L->verts, (size_t)V));
+    if (V > 0) {
+        CUDA_TRY(cudaMemcpyAsync(L->verts, verts, sizeof(double2) * (size_t)V, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(launch_check_finite(L->verts, (int)V, dbad, s));
+    }
+    int bad = 0;
+    st = read_flag(dbad, s, &bad);
+    if (st != SJ_OK) return st;
+    if (bad) return fail(SJ_ERR_INVALID, "invalid polygon layer (offsets, ring sizes or non-finite vertex)");
+    CUDA_TRY(dalloc(&L->obj_voff, (size_t)P + 1));
+    CUDA_TRY(dalloc(&L->nxt, (size_t)V));
+    CUDA_TRY(dalloc(&L->vsplit, (size_t)V));
+    CUDA_TRY(launch_pip_topology(L->ring_off, (int)R, L->poly_ring_off, P, L->obj_voff, L->nxt, s));
+    if (V > 0) CUDA_TRY(launch_split(L->verts, (int)V, L->vsplit, s));
+    CUDA_TRY(dalloc(&L->stats, ST_N));
+    CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));
+    st = build_candidates(L, dbad, s);
+    if (st != SJ_OK) return st;
+    *out = L;
+    guard.L = nullptr;
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_p2p_layer_create(const double *verts, int64_t V, const int64_t *line_off, int32_t Lc, double D,
+                                         const sj_grid *g, void *stream, sj_layer **out) {
+    DevInfo *di;
+    sj_status st = layer_common_checks(verts, V, g, stream, out, &di);
+    if (st != SJ_OK) return st;
+    if (Lc < 0) return fail(SJ_ERR_INVALID, "polyline count out of range");
+    if (!line_off) return fail(SJ_ERR_INVALID, "line_off is NULL");
+    if (!(std::isfinite(D) && D >= 0.0)) return fail(SJ_ERR_INVALID, "D must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    LayerGuard guard{new sj_layer()};
+    sj_layer *L = guard.L;
+    L->kind = KIND_P2P;
+    CUDA_TRY(cudaGetDevice(&L->device));
+    L->grid = *g;
+    L->g = make_grid(g);
+    L->nobj = Lc;
+    L->V = (int)V;
+    L->R = Lc;
+    L->D = D;
+    int *dbad = nullptr;
+    CUDA_TRY(dalloc(&dbad, 1));
+    struct F { int *p; ~F() { cudaFree(p); } } fbad{dbad};
+    CUDA_TRY(cudaMemsetAsync(dbad, 0, sizeof(int), s));
+    CUDA_TRY(dalloc(&L->obj_voff, (size_t)Lc + 1));
+    CUDA_TRY(launch_check_offsets(line_off, Lc, 1, 0, V, L->obj_voff, dbad, s));
+    CUDA_TRY(dalloc(&L->verts, (size_t)V));
+    if (V > 0) {
+        CUDA_TRY(cudaMemcpyAsync(L->verts, verts, sizeof(double2) * (size_t)V, cudaMemcpyDeviceToDevice, s));
+        CUDA_TRY(launch_check_finite(L->verts, (int)V, dbad, s));
+    }
+    int bad = 0;
+    st = read_flag(dbad, s, &bad);
+    if (st != SJ_OK) return st;
+    if (bad) return fail(SJ_ERR_INVALID, "invalid polyline layer (offsets or non-finite vertex)");
+    CUDA_TRY(dalloc(&L->vsplit, (size_t)V));
+    CUDA_TRY(dalloc(&L->seg_e64, (size_t)V));
+    CUDA_TRY(dalloc(&L->seg_inv64, (size_t)V));
+    CUDA_TRY(dalloc(&L->seg_e32, (size_t)V));
+    CUDA_TRY(dalloc(&L->seg_inv32, (size_t)V));
+    if (V > 0) {
+        CUDA_TRY(launch_split(L->verts, (int)V, L->vsplit, s));
+        CUDA_TRY(launch_seg_table(L->verts, L->obj_voff, Lc, L->seg_e64, L->seg_inv64, L->seg_e32, L->seg_inv32, s));
+    }
+    CUDA_TRY(dalloc(&L->stats, ST_N));
+    CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));
+    st = build_candidates(L, dbad, s);
+    if (st != SJ_OK) return st;
+    *out = L;
+    guard.L = nullptr;
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_layer_destroy(sj_layer *L) {
+    if (!L) return SJ_OK;
+    cudaDeviceSynchronize();
+    layer_free(L);
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_layer_get_info(const sj_layer *L, sj_layer_info *out) {
+    if (!L || !out) return fail(SJ_ERR_INVALID, "NULL argument");
+    out->kind = L->kind;
+    out->n_objects = L->nobj;
+    out->n_vertices = L->V;
+    out->n_rings = L->R;
+    out->n_cells = L->g.G;
+    out->n_candidates = L->M;
+    out->D = L->D;
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_layer_get_candidates(const sj_layer *L, int32_t *cand_start, int32_t *cand_ids) {
+    if (!L || !cand_start || (!cand_ids && L->M > 0)) return fail(SJ_ERR_INVALID, "NULL argument");
+    CUDA_TRY(cudaMemcpy(cand_start, L->cand_start, sizeof(int) * ((size_t)L->g.G + 1), cudaMemcpyDeviceToHost));
+    if (L->M > 0) CUDA_TRY(cudaMemcpy(cand_ids, L->cand_ids, sizeof(int) * (size_t)L->M, cudaMemcpyDeviceToHost));
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_layer_get_stats(const sj_layer *L, sj_run_stats *out) {
+    if (!L || !out) return fail(SJ_ERR_INVALID, "NULL argument");
+    unsigned long long h[ST_N];
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(h, L->stats, sizeof(h), cudaMemcpyDeviceToHost));
+    resolve_events(L);
+    out->refine_launches = L->refine_launches;
+    out->refine_ms = L->refine_ms;
+    out->joins = L->joins.load();
+    out->points = L->points.load();
+    out->items = (int64_t)h[ST_ITEMS];
+    out->pairs = (int64_t)h[ST_PAIRS];
+    out->edge_tests = (int64_t)h[ST_TESTS];
+    out->fallbacks = (int64_t)h[ST_FALLBACK];
+    out->hits = (int64_t)h[ST_HITS];
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_layer_reset_stats(sj_layer *L) {
+    if (!L) return fail(SJ_ERR_INVALID, "NULL argument");
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemset(L->stats, 0, sizeof(unsigned long long) * ST_N));
+    resolve_events(L);
+    L->refine_ms = 0.0;
+    L->refine_launches = 0;
+    L->joins = 0;
+    L->points = 0;
+    return SJ_OK;
+}
+
+// ------------------------------------------------------------------ joins
+
+struct JoinBufs {
+    int *cnt, *cell_start, *perm, *totals;
+    int2 *key_rank, *items, *block_sums, *fb;
+    double2 *spts;
+};
+
+static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb) {
+    size_t max_items = (size_t)(N / ch) + (size_t)std::min<int64_t>(G, N) + 1;
+    b.cnt = s.take<int>((size_t)G + 1);
+    b.cell_start = s.take<int>((size_t)G + 1);
+    b.totals = s.take<int>(4);
+    b.key_rank = s.take<int2>((size_t)N);
+    b.perm = s.take<int>((size_t)N);
+    b.spts = s.take<double2>((size_t)N);
+    b.items = s.take<int2>(max_items);
+    b.block_sums = s.take<int2>(bucket_scan_blocks(G));
+    b.fb = need_fb ? s.take<int2>((size_t)N) : nullptr;
+}
+
+static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                           const sj_opts *o, void *stream) {
+    if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
+    if (L->kind != kind) return fail(SJ_ERR_INVALID, kind == KIND_PIP ? "not a polygon layer" : "not a polyline layer");
+    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
+    if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
+    int form = o ? o->form : SJ_FP64;
+    if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
+    int launch = o ? o->launch : SJ_PER_REQUEST;
+    if (launch != SJ_PER_REQUEST && launch != SJ_PERSISTENT) return fail(SJ_ERR_INVALID, "unknown launch form");
+    int ch = (o && o->pts_per_item) ? o->pts_per_item : 64;
+    if (ch < 1 || ch > MAX_CH) return fail(SJ_ERR_INVALID, "pts_per_item must be in 1..128");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != L->device) return fail(SJ_ERR_INVALID, "layer belongs to another device");
+    DevInfo *di;
+    sj_status st = device_info(dev, &di);
+    if (st != SJ_OK) return st;
+    L->joins++;
+    L->points += N;
+    if (N == 0) return SJ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int G = L->g.G;
+    const bool need_fb = (kind == KIND_P2P && form == SJ_FP32X);
+
+    JoinBufs b;
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb); });
+    Scratch sc;
+    CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
+    carve(sc, b, N, G, ch, need_fb);
+    cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * ((size_t)G + 1), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
+
+    BucketArgs ba{};
+    ba.g = L->g;
+    ba.pts = (const double2 *)pts;
+    ba.n = (int)N;
+    ba.cnt = b.cnt;
+    ba.key_rank = b.key_rank;
+    ba.cell_start = b.cell_start;
+    ba.perm = b.perm;
+    ba.spts = b.spts;
+    ba.cand_start = L->cand_start;
+    ba.ch = ch;
+    ba.items = b.items;
+    ba.block_sums = b.block_sums;
+    ba.totals = b.totals;
+    ba.out_id = out_id;
+    ba.out_d = kind == KIND_P2P ? out_d : nullptr;
+    if (e == cudaSuccess) e = launch_bucket(ba, s);
+
+    RefineArgs ra{};
+    ra.g = L->g;
+    ra.items = b.items;
+    ra.n_items = b.totals + 1;
+    ra.cell_start = b.cell_start;
+    ra.perm = b.perm;
+    ra.spts = b.spts;
+    ra.cand_start = L->cand_start;
+    ra.cand_ids = L->cand_ids;
+    ra.obj_voff = L->obj_voff;
+    ra.nxt = L->nxt;
+    ra.verts = L->verts;
+    ra.vsplit = L->vsplit;
+    ra.seg_e64 = L->seg_e64;
+    ra.seg_inv64 = L->seg_inv64;
+    ra.seg_e32 = L->seg_e32;
+    ra.seg_inv32 = L->seg_inv32;
+    ra.D = L->D;
+    ra.eps_abs = L->eps_abs;
+    ra.ch = ch;
+    ra.out_id = out_id;
+    ra.out_d = out_d;
+    ra.fb = b.fb;
+    ra.n_fb = b.totals + 2;
+    ra.stats = L->stats;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    const bool timed = o && (o->flags & SJ_FLAG_TIME_REFINE);
+    if (e == cudaSuccess && timed) {
+        e = cudaEventCreate(&ev0);
+        if (e == cudaSuccess) e = cudaEventCreate(&ev1);
+        if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
+    }
+    if (e == cudaSuccess) {
+        if (kind == KIND_PIP) {
+            e = launch_pip_refine(ra, form, 4, di->sms * di->pip_bps[form], s);
+        } else {
+            e = launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s);
+            if (e == cudaSuccess && need_fb) e = launch_p2p_recheck(ra, di->sms * 4, s);
+        }
+    }
+    if (timed && ev1) {
+        if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
+        std::lock_guard<std::mutex> lk(L->ev_mu);
+        L->ev_pending.emplace_back(ev0, ev1);
+    }
+    cudaError_t e2 = cudaFreeAsync(sc.base, s);
+    if (e != cudaSuccess) return cuda_fail(e, "join launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_pip_join(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, const sj_opts *o,
+                                 void *stream) {
+    return join_impl(L, KIND_PIP, pts, N, out_id, nullptr, o, stream);
+}
+
+extern "C" sj_status sj_p2p_join(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                                 const sj_opts *o, void *stream) {
+    return join_impl(L, KIND_P2P, pts, N, out_id, out_d, o, stream);
+}
+
+static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                           const sj_opts *o, void *stream) {
+    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (N == 0) return join_impl(L, kind, nullptr, 0, nullptr, nullptr, o, stream);
+    char *d = nullptr;
+    size_t bp = (size_t)N * 16, bi = ((size_t)N * 4 + 255) & ~(size_t)255, bd = out_d ? (size_t)N * 8 : 0;
+    CUDA_TRY(cudaMallocAsync((void **)&d, bp + bi + bd, s));
+    double *dp = (double *)d;
+    int32_t *di = (int32_t *)(d + bp);
+    double *dd = out_d ? (double *)(d + bp + bi) : nullptr;
+    sj_status st = SJ_OK;
+    cudaError_t e = cudaMemcpyAsync(dp, pts, bp, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+        st = join_impl(L, kind, dp, N, di, dd, o, stream);
+        if (st == SJ_OK) {
+            e = cudaMemcpyAsync(out_id, di, (size_t)N * 4, cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess && out_d) e = cudaMemcpyAsync(out_d, dd, (size_t)N * 8, cudaMemcpyDeviceToHost, s);
+        }
+    }
+    cudaFreeAsync(d, s);
+    cudaError_t e3 = cudaStreamSynchronize(s);
+    if (st != SJ_OK) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "host join copy");
+    if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_pip_join_host(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id,
+                                      const sj_opts *o, void *stream) {
+    return join_host(L, KIND_PIP, pts, N, out_id, nullptr, o, stream);
+}
+
+extern "C" sj_status sj_p2p_join_host(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                                      const sj_opts *o, void *stream) {
+    return join_host(L, KIND_P2P, pts, N, out_id, out_d, o, stream);
+}
+
+extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32_t *cell_start, int32_t *perm,
+                                      void *stream) {
+    if (!grid_ok(g)) return fail(SJ_ERR_INVALID, "invalid grid");
+    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (!cell_start || (N > 0 && (!pts || !perm))) return fail(SJ_ERR_INVALID, "NULL buffer");
+    if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    GridDev gd = make_grid(g);
+    Scratch sc;
+    auto lay = [&](Scratch &x, int **cnt, int **totals, int2 **kr, int2 **bs) {
+        *cnt = x.take<int>((size_t)gd.G + 1);
+        *totals = x.take<int>(4);
+        *kr = x.take<int2>((size_t)N);
+        *bs = x.take<int2>(bucket_scan_blocks(gd.G));
+    };
+    int *cnt, *totals;
+    int2 *kr, *bs;
+    size_t bytes = measure([&](Scratch &x) { lay(x, &cnt, &totals, &kr, &bs); });
+    CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
+    lay(sc, &cnt, &totals, &kr, &bs);
+    BucketArgs ba{};
+    ba.g = gd;
+    ba.pts = (const double2 *)pts;
+    ba.n = (int)N;
+    ba.cnt = cnt;
+    ba.key_rank = kr;
+    ba.cell_start = cell_start;
+    ba.perm = perm;
+    ba.block_sums = bs;
+    ba.totals = totals;
+    ba.ch = 1;
+    cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)gd.G + 1), s);
+    if (e == cudaSuccess) e = launch_bucket(ba, s);
+    cudaError_t e2 = cudaFreeAsync(sc.base, s);
+    if (e != cudaSuccess) return cuda_fail(e, "bucket launch");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    return SJ_OK;
+}
+
+extern "C" const char *sj_last_error(void) { return g_err.c_str(); }
+
+extern "C" const char *sj_version(void) { return "sj 0.1 (sm_103a)"; }

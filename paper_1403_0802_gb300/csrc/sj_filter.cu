@@ -1,0 +1,414 @@
+// sj_filter.cu -- the uniform-grid filter of Sec. III.A (Fig. 1):
+//   - point bucketing: cell id per point, per-cell counts, exclusive scan,
+//     scatter into cell order (the VGC / VGI vectors of Fig. 1), plus the
+//     (cell, point-chunk) work items of cells that have candidates;
+//   - layer side: per-object MBB, rasterisation of (expanded) MBBs to cells,
+//     and the per-cell candidate lists (the VPP relation) in CSR form.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+
+// ------------------------------------------------------------------ block scan helpers
+
+constexpr int SCAN_T = 256;
+constexpr int SCAN_V = 16;
+constexpr int SCAN_TILE = SCAN_T * SCAN_V;
+
+__device__ __forceinline__ int2 add2(int2 a, int2 b) { return make_int2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ int2 sub2(int2 a, int2 b) { return make_int2(a.x - b.x, a.y - b.y); }
+
+__device__ __forceinline__ int2 warp_incl_scan(int2 v) {
+    int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int x = __shfl_up_sync(FULL, v.x, o), y = __shfl_up_sync(FULL, v.y, o);
+        if (lane >= o) { v.x += x; v.y += y; }
+    }
+    return v;
+}
+
+// Inclusive scan over the block (blockDim.x = NT, a multiple of 32); also
+// returns the block total.
+template <int NT>
+__device__ __forceinline__ int2 block_incl_scan(int2 v, int2 &total) {
+    __shared__ int2 wsum[NT / 32];
+    int lane = lane_id(), w = threadIdx.x >> 5;
+    int2 inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        int2 s = lane < NT / 32 ? wsum[lane] : make_int2(0, 0);
+        s = warp_incl_scan(s);
+        if (lane < NT / 32) wsum[lane] = s;
+    }
+    __syncthreads();
+    if (w > 0) inc = add2(inc, wsum[w - 1]);
+    total = wsum[NT / 32 - 1];
+    __syncthreads();
+    return inc;
+}
+
+// Phase 1: per-tile sums.
+template <class Load>
+__global__ void __launch_bounds__(SCAN_T) k_scan_reduce(Load ld, int n, int2 *block_sums) {
+    int base = blockIdx.x * SCAN_TILE;
+    int2 s = make_int2(0, 0);
+    for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
+        int c = base + k;
+        if (c < n) s = add2(s, ld(c));
+    }
+    int2 total;
+    block_incl_scan<SCAN_T>(s, total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// Phase 2: exclusive scan of the tile sums in one block; block_sums[nb] and
+// totals[0..1] get the grand total.
+__global__ void __launch_bounds__(1024) k_scan_top(int2 *block_sums, int nb, int *totals) {
+    int2 carry = make_int2(0, 0);
+    for (int base = 0; base < nb; base += 1024) {
+        int i = base + threadIdx.x;
+        int2 v = i < nb ? block_sums[i] : make_int2(0, 0);
+        int2 total;
+        int2 inc = block_incl_scan<1024>(v, total);
+        if (i < nb) block_sums[i] = add2(carry, sub2(inc, v));
+        carry = add2(carry, total);
+    }
+    if (threadIdx.x == 0) {
+        block_sums[nb] = carry;
+        if (totals) { totals[0] = carry.x; totals[1] = carry.y; }
+    }
+}
+
+// Phase 3: rescan each tile with its offset; ap(c, exclusive prefix, value).
+template <class Load, class Apply>
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply(Load ld, Apply ap, int n, const int2 *block_sums) {
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+    int2 v[SCAN_V];
+    int2 tsum = make_int2(0, 0);
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+        int c = base + j;
+        v[j] = c < n ? ld(c) : make_int2(0, 0);
+        tsum = add2(tsum, v[j]);
+    }
+    int2 total;
+    int2 inc = block_incl_scan<SCAN_T>(tsum, total);
+    int2 ex = add2(sub2(inc, tsum), block_sums[blockIdx.x]);
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+        int c = base + j;
+        if (c < n) ap(c, ex, v[j], n);
+        ex = add2(ex, v[j]);
+    }
+}
+
+template <class Load, class Apply>
+static cudaError_t run_scan(Load ld, Apply ap, int n, int2 *block_sums, int *totals, cudaStream_t s) {
+    int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (nb == 0) nb = 1;
+    k_scan_reduce<Load><<<nb, SCAN_T, 0, s>>>(ld, n, block_sums);
+    k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, totals);
+    k_scan_apply<Load, Apply><<<nb, SCAN_T, 0, s>>>(ld, ap, n, block_sums);
+    return cudaGetLastError();
+}
+
+size_t bucket_scan_blocks(int G) { return (size_t)((G + SCAN_TILE - 1) / SCAN_TILE) + 2; }
+
+// Loader / writer for a plain int array -> exclusive offsets (with the total in out[n]).
+struct IntLoad {
+    const int *a;
+    __device__ int2 operator()(int c) const { return make_int2(a[c], 0); }
+};
+struct OffsetApply {
+    int *out;
+    __device__ void operator()(int c, int2 ex, int2 v, int n) const {
+        out[c] = ex.x;
+        if (c == n - 1) out[n] = ex.x + v.x;
+    }
+};
+
+// ------------------------------------------------------------------ point bucketing
+
+// a1: cell id per point and per-cell count; the atomic's return value is the
+// point's rank inside its cell, so the scatter needs no second pass.  The
+// outputs are initialised here (-1 / +inf), refinement overwrites the hits.
+__global__ void k_cell_hist(BucketArgs a) {
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        double2 p = a.pts[i];
+        int c = point_cell(a.g, p.x, p.y);
+        int r = 0;
+        if (c < a.g.G) r = atomicAdd(&a.cnt[c], 1);
+        a.key_rank[i] = make_int2(c, r);
+        if (a.out_id) a.out_id[i] = -1;
+        if (a.out_d) a.out_d[i] = inf;
+    }
+}
+
+// Per cell: (points, work items).  A cell yields ceil(points / ch) items when
+// it has both points and candidates.
+struct BucketLoad {
+    const int *cnt;
+    const int *cand_start;
+    int ch;
+    __device__ int2 operator()(int c) const {
+        int np = cnt[c];
+        int ni = 0;
+        if (cand_start && np > 0 && cand_start[c + 1] > cand_start[c]) ni = (np + ch - 1) / ch;
+        return make_int2(np, ni);
+    }
+};
+struct BucketApply {
+    int *cell_start;
+    int2 *items;
+    int ch;
+    __device__ void operator()(int c, int2 ex, int2 v, int n) const {
+        cell_start[c] = ex.x;
+        if (c == n - 1) cell_start[n] = ex.x + v.x;
+        if (items)
+            for (int t = 0; t < v.y; ++t) items[ex.y + t] = make_int2(c, t * ch);
+    }
+};
+
+__global__ void k_scatter(BucketArgs a) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
+        int2 k = a.key_rank[i];
+        if (k.x < a.g.G) {
+            int pos = a.cell_start[k.x] + k.y;
+            a.perm[pos] = i;
+            if (a.spts) a.spts[pos] = a.pts[i];
+        }
+    }
+}
+
+static int stream_blocks(long long n, int per_block, int cap) {
+    long long b = (n + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (int)b;
+}
+
+cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s) {
+    int nb = stream_blocks(a.n, 256, 152 * 32);
+    k_cell_hist<<<nb, 256, 0, s>>>(a);
+    cudaError_t e = run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch},
+                             a.g.G, a.block_sums, a.totals, s);
+    if (e != cudaSuccess) return e;
+    k_scatter<<<nb, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ layer build
+
+// Offsets must start at `first`, end at `last`, and give runs of at least
+// `min_size`; a copy narrowed to int32 is written to out.
+__global__ void k_check_offsets(const int64_t *off, int64_t n, int64_t min_size, int64_t first, int64_t last,
+                                int *out, int *bad) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k <= n; k += (int64_t)gridDim.x * blockDim.x) {
+        int64_t v = off[k];
+        if (k == 0 && v != first) atomicOr(bad, 1);
+        if (k == n && v != last) atomicOr(bad, 1);
+        if (k < n && off[k + 1] - v < min_size) atomicOr(bad, 1);
+        if (v < 0 || v > 2147483647LL) atomicOr(bad, 1);
+        if (out) out[k] = (int)v;
+    }
+}
+
+__global__ void k_check_finite(const double2 *v, int n, int *bad) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double2 p = v[i];
+        if (!(isfinite(p.x) && isfinite(p.y))) atomicOr(bad, 1);
+    }
+}
+
+// Vertex range of polygon p = rings poly_ring_off[p] .. poly_ring_off[p + 1].
+__global__ void k_poly_voff(const int *ring_off, const int *poly_ring_off, int P, int *poly_voff) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p <= P; p += gridDim.x * blockDim.x)
+        poly_voff[p] = ring_off[poly_ring_off[p]];
+}
+
+// Next vertex within the same ring (closing edge wraps to the ring start).
+__global__ void k_ring_next(const int *ring_off, int R, int *nxt) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+        int b = ring_off[r], e = ring_off[r + 1];
+        for (int i = b; i < e; ++i) nxt[i] = (i + 1 < e) ? i + 1 : b;
+    }
+}
+
+// (hi, lo) FP32 split of each vertex: hi = fl32(x), lo = fl32(x - hi).
+__global__ void k_split(const double2 *v, int n, float4 *vs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        double2 p = v[i];
+        float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
+        float xl = __double2float_rn(__dsub_rn(p.x, (double)xh));
+        float yl = __double2float_rn(__dsub_rn(p.y, (double)yh));
+        vs[i] = make_float4(xh, yh, xl, yl);
+    }
+}
+
+// P2P segment table: for the segment that starts at vertex i of polyline l,
+// e = v[i+1] - v[i] and 1 / |e|^2 (0 for a zero-length segment, and for the
+// single vertex of a one-vertex polyline, which then acts as a point).
+__global__ void k_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
+                            float *inv32) {
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
+        int b = line_off[l], e = line_off[l + 1];
+        for (int i = b; i < e; ++i) {
+            double ex = 0.0, ey = 0.0, inv = 0.0;
+            if (i + 1 < e) {
+                ex = __dsub_rn(v[i + 1].x, v[i].x);
+                ey = __dsub_rn(v[i + 1].y, v[i].y);
+                double L2 = __dadd_rn(__dmul_rn(ex, ex), __dmul_rn(ey, ey));
+                inv = L2 > 0.0 ? __ddiv_rn(1.0, L2) : 0.0;
+            }
+            e64[i] = make_double2(ex, ey);
+            inv64[i] = inv;
+            e32[i] = make_float2(__double2float_rn(ex), __double2float_rn(ey));
+            inv32[i] = __double2float_rn(inv);
+        }
+    }
+}
+
+// a3: MBB per object, one warp per object; flags an MBB outside the closed
+// grid box (bit 2 of *bad).
+__global__ void k_mbb(LayerBuildArgs a) {
+    int lane = lane_id();
+    int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int o = warp; o < a.nobj; o += nwarps) {
+        int b = a.obj_voff[o], e = a.obj_voff[o + 1];
+        double xmin = INFINITY, ymin = INFINITY, xmax = -INFINITY, ymax = -INFINITY;
+        for (int i = b + lane; i < e; i += 32) {
+            double2 p = a.verts[i];
+            xmin = fmin(xmin, p.x); xmax = fmax(xmax, p.x);
+            ymin = fmin(ymin, p.y); ymax = fmax(ymax, p.y);
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            xmin = fmin(xmin, __shfl_xor_sync(FULL, xmin, s));
+            ymin = fmin(ymin, __shfl_xor_sync(FULL, ymin, s));
+            xmax = fmax(xmax, __shfl_xor_sync(FULL, xmax, s));
+            ymax = fmax(ymax, __shfl_xor_sync(FULL, ymax, s));
+        }
+        if (lane == 0) {
+            a.mbb[o] = Box{xmin, ymin, xmax, ymax};
+            if (!(xmin >= a.g.x0 && xmax <= a.g.x1 && ymin >= a.g.y0 && ymax <= a.g.y1)) atomicOr(a.bad, 2);
+        }
+    }
+}
+
+// Largest double below x / smallest above x (x not NaN; infinities kept).
+__device__ __forceinline__ double next_down(double x) {
+    if (isinf(x)) return x;
+    if (x == 0.0) return -4.9406564584124654e-324;
+    long long b = __double_as_longlong(x);
+    return __longlong_as_double(x > 0.0 ? b - 1 : b + 1);
+}
+__device__ __forceinline__ double next_up(double x) { return -next_down(-x); }
+
+// a4: cell box of an MBB (P2P: widened by D and rounded outward by one ulp).
+__device__ __forceinline__ int4 mbb_cell_box(const LayerBuildArgs &a, Box m) {
+    double xlo = m.xmin, ylo = m.ymin, xhi = m.xmax, yhi = m.ymax;
+    if (a.kind == KIND_P2P) {
+        xlo = next_down(__dsub_rn(xlo, a.D));
+        ylo = next_down(__dsub_rn(ylo, a.D));
+        xhi = next_up(__dadd_rn(xhi, a.D));
+        yhi = next_up(__dadd_rn(yhi, a.D));
+    }
+    return make_int4(clamped_axis(xlo, a.g.x0, a.g.cw, a.g.nx), clamped_axis(ylo, a.g.y0, a.g.ch, a.g.ny),
+                     clamped_axis(xhi, a.g.x0, a.g.cw, a.g.nx), clamped_axis(yhi, a.g.y0, a.g.ch, a.g.ny));
+}
+
+__global__ void k_raster_count(LayerBuildArgs a, unsigned long long *total) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.nobj; o += gridDim.x * blockDim.x) {
+        int4 b = mbb_cell_box(a, a.mbb[o]);
+        long long n = (long long)(b.z - b.x + 1) * (long long)(b.w - b.y + 1);
+        a.obj_cells[o] = n > 2147483647LL ? 2147483647 : (int)n;
+        atomicAdd(total, (unsigned long long)n);
+    }
+}
+
+// Emit (cell, object) pairs and count candidates per cell.
+__global__ void k_raster_emit(LayerBuildArgs a, int2 *pairs) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < a.nobj; o += gridDim.x * blockDim.x) {
+        int4 b = mbb_cell_box(a, a.mbb[o]);
+        int k = a.obj_cells[o];
+        for (int iy = b.y; iy <= b.w; ++iy)
+            for (int ix = b.x; ix <= b.z; ++ix) {
+                int c = iy * a.g.nx + ix;
+                pairs[k++] = make_int2(c, o);
+                atomicAdd(&a.cell_cnt[c], 1);
+            }
+    }
+}
+
+__global__ void k_cand_scatter(LayerBuildArgs a, const int2 *pairs, int M, int *cand_ids) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        int2 p = pairs[k];
+        cand_ids[a.cand_start[p.x] + atomicAdd(&a.cursor[p.x], 1)] = p.y;
+    }
+}
+
+// Sort each cell's candidate ids ascending (insertion sort; lists are short).
+__global__ void k_cand_sort(const int *cand_start, int G, int *cand_ids) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
+        int b = cand_start[c], e = cand_start[c + 1];
+        for (int i = b + 1; i < e; ++i) {
+            int v = cand_ids[i], j = i - 1;
+            while (j >= b && cand_ids[j] > v) { cand_ids[j + 1] = cand_ids[j]; --j; }
+            cand_ids[j + 1] = v;
+        }
+    }
+}
+
+// Host side of the layer build steps that the API file sequences.
+cudaError_t launch_check_offsets(const int64_t *off, int64_t n, int64_t min_size, int64_t first, int64_t last, int *out,
+                                 int *bad, cudaStream_t s) {
+    k_check_offsets<<<stream_blocks(n + 1, 256, 4096), 256, 0, s>>>(off, n, min_size, first, last, out, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_check_finite(const double2 *v, int n, int *bad, cudaStream_t s) {
+    k_check_finite<<<stream_blocks(n, 256, 4096), 256, 0, s>>>(v, n, bad);
+    return cudaGetLastError();
+}
+cudaError_t launch_pip_topology(const int *ring_off, int R, const int *poly_ring_off, int P, int *poly_voff, int *nxt,
+                                cudaStream_t s) {
+    k_poly_voff<<<stream_blocks(P + 1, 256, 4096), 256, 0, s>>>(ring_off, poly_ring_off, P, poly_voff);
+    k_ring_next<<<stream_blocks(R, 128, 4096), 128, 0, s>>>(ring_off, R, nxt);
+    return cudaGetLastError();
+}
+cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s) {
+    k_split<<<stream_blocks(n, 256, 4096), 256, 0, s>>>(v, n, vs);
+    return cudaGetLastError();
+}
+cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
+                             float *inv32, cudaStream_t s) {
+    k_seg_table<<<stream_blocks(L, 128, 4096), 128, 0, s>>>(v, line_off, L, e64, inv64, e32, inv32);
+    return cudaGetLastError();
+}
+cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s) {
+    k_mbb<<<stream_blocks((long long)a.nobj * 32, 256, 4096), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *total, cudaStream_t s) {
+    k_raster_count<<<stream_blocks(a.nobj, 256, 4096), 256, 0, s>>>(a, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // Counts -> exclusive offsets in place: every tile loads its counts into
+    // registers before it writes, and tiles write only their own indices.
+    return run_scan(IntLoad{a.obj_cells}, OffsetApply{a.obj_cells}, a.nobj, a.block_sums, a.totals, s);
+}
+cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s) {
+    k_raster_emit<<<stream_blocks(a.nobj, 128, 4096), 128, 0, s>>>(a, pairs);
+    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{a.cand_start}, a.g.G, a.block_sums, a.totals, s);
+    if (e != cudaSuccess) return e;
+    k_cand_scatter<<<stream_blocks(M, 256, 4096), 256, 0, s>>>(a, pairs, M, cand_ids);
+    k_cand_sort<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(a.cand_start, a.g.G, cand_ids);
+    return cudaGetLastError();
+}
+
+}  // namespace sj

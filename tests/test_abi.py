@@ -1,0 +1,69 @@
+"""Host-side checks of the C ABI (no GPU needed): libsj.so builds for sm_103a,
+loads, and exports every entry point include/sj.h declares; the Python
+binding declares exactly those signatures."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "sj.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sj_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libsj():
+    from paper_1403_0802_gb300 import build
+    so = build.build()
+    return C.CDLL(so)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("sj_pip_layer_create", "sj_p2p_layer_create", "sj_pip_join", "sj_p2p_join", "sj_layer_destroy",
+                 "sj_bucket_points", "sj_last_error"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(libsj):
+    missing = [n for n in declared_functions() if not hasattr(libsj, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_the_header(libsj):
+    from paper_1403_0802_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == declared_functions()
+
+
+def test_version_and_error_string_without_gpu(libsj):
+    libsj.sj_version.restype = C.c_char_p
+    libsj.sj_last_error.restype = C.c_char_p
+    assert b"sm_103a" in libsj.sj_version()
+    assert libsj.sj_last_error() == b""
+
+
+def test_argument_errors_are_synchronous_and_need_no_gpu(libsj):
+    """Argument checks run before any CUDA call: a bad grid is rejected."""
+    from paper_1403_0802_gb300 import _lib
+    lib = _lib.lib()
+    bad = _lib.sj_grid(0.0, 0.0, -1.0, 1.0, 4, 4)       # x1 < x0
+    h = C.c_void_p()
+    st = lib.sj_p2p_layer_create(None, 0, None, 0, 1.0, C.byref(bad), None, C.byref(h))
+    assert st == _lib.SJ_ERR_INVALID
+    assert b"grid" in lib.sj_last_error()
+    st = lib.sj_bucket_points(None, 0, C.byref(bad), None, None, None)
+    assert st == _lib.SJ_ERR_INVALID
+
+
+def test_struct_layouts_match_header():
+    from paper_1403_0802_gb300 import _lib
+    assert C.sizeof(_lib.sj_grid) == 40
+    assert C.sizeof(_lib.sj_opts) == 24
+    assert C.sizeof(_lib.sj_run_stats) == 72
+    assert C.sizeof(_lib.sj_layer_info) == 48

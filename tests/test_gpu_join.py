@@ -1,0 +1,346 @@
+"""GPU parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+PIP ids and the filter's candidate lists must match the oracle bit for bit in
+both arithmetic forms.  P2P ids must match except where the oracle's best and
+second-best distances tie within 1e-9 (relative) or the best distance sits
+within 1e-9 of D; FP64 distances must agree to 1e-12 * max(d, 1 m); FP32X
+distances must stay inside the per-point bound the kernel certifies
+(64 * 2^-24 * the largest cell-relative coordinate involved, plus 1e-9 m).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1403_0802_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FORMS = ("fp64", "fp32x")
+
+
+@pytest.fixture(scope="module")
+def api():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0802_gb300 import api as A
+    from paper_1403_0802_gb300 import build
+    build.build()
+    return A
+
+
+# ------------------------------------------------------------------ helpers
+
+def pip_ref(oracle, w):
+    P = w.polygons
+    return oracle.pip_join(w.grid, w.points, P.verts, P.ring_off, P.poly_ring_off)
+
+
+def fp32x_bound(oracle, g, pts, mbb, cs, ci):
+    """64 u times the largest |coordinate - cell corner| among the point and the
+    MBB corners of its cell's candidates, plus 1e-9 m."""
+    cells = oracle.point_cells(g, pts)
+    G = g["nx"] * g["ny"]
+    cw = (g["x1"] - g["x0"]) / g["nx"]
+    ch = (g["y1"] - g["y0"]) / g["ny"]
+    inside = cells < G
+    c = np.where(inside, cells, 0)
+    ox = g["x0"] + (c % g["nx"]) * cw
+    oy = g["y0"] + (c // g["nx"]) * ch
+    # per cell: max over candidates of the MBB extremes
+    counts = np.diff(cs)
+    xlo = np.full(G, np.inf); xhi = np.full(G, -np.inf); ylo = np.full(G, np.inf); yhi = np.full(G, -np.inf)
+    if len(ci):
+        ne = np.flatnonzero(counts > 0)
+        starts = cs[:-1][ne]
+        xlo[ne] = np.minimum.reduceat(mbb[ci, 0], starts)
+        xhi[ne] = np.maximum.reduceat(mbb[ci, 2], starts)
+        ylo[ne] = np.minimum.reduceat(mbb[ci, 1], starts)
+        yhi[ne] = np.maximum.reduceat(mbb[ci, 3], starts)
+    m = np.maximum.reduce([np.abs(pts[:, 0] - ox), np.abs(pts[:, 1] - oy), np.abs(xlo[c] - ox), np.abs(xhi[c] - ox),
+                           np.abs(ylo[c] - oy), np.abs(yhi[c] - oy)])
+    m = np.where(np.isfinite(m), m, 0.0)
+    return 64.0 * 2.0 ** -24 * m * 1.0001 + 1e-9
+
+
+def check_p2p(oracle, w, gid, gd, form, verts=None, line_off=None):
+    L = w.polylines if verts is None else None
+    verts = L.verts if verts is None else verts
+    line_off = L.line_off if line_off is None else line_off
+    rid, rd, d1, d2 = oracle.p2p_join(w.grid, w.points, verts, line_off, w.D)
+    tie = (d2 - d1) <= 1e-9 * np.maximum(d1, 1.0)
+    edge = np.abs(d1 - w.D) <= 1e-9 * max(w.D, 1.0)
+    bad = np.flatnonzero((gid != rid) & ~tie & ~edge)
+    assert bad.size == 0, (form, bad[:5], gid[bad[:5]], rid[bad[:5]], gd[bad[:5]], rd[bad[:5]])
+    miss = gid < 0
+    assert np.all(np.isinf(gd[miss]))
+    both = (gid >= 0) & (rid >= 0)
+    err = np.abs(gd[both] - rd[both])
+    if form == "fp64":
+        lim = 1e-12 * np.maximum(rd[both], 1.0)
+    else:
+        mbb = oracle.p2p_mbb(w.grid, verts, line_off)
+        cs, ci = oracle.cand_csr(w.grid, mbb, w.D, expand=True)
+        lim = fp32x_bound(oracle, w.grid, w.points, mbb, cs, ci)[both]
+    worst = np.flatnonzero(err > lim)
+    assert worst.size == 0, (form, err[worst[:5]], lim[worst[:5]])
+    return {"hit_frac": float((gid >= 0).mean()), "max_abs_err": float(err.max()) if err.size else 0.0}
+
+
+def to_np(t):
+    return t.cpu().numpy()
+
+
+# ------------------------------------------------------------------ filter
+
+def test_candidate_lists_match_oracle(api, oracle):
+    w = synth.pip_stars(n_points=10)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        gs, gi = layer.candidates()
+        info = layer.info()
+    mbb = oracle.pip_mbb(w.grid, P.verts, P.ring_off, P.poly_ring_off)
+    rs, ri = oracle.cand_csr(w.grid, mbb)
+    np.testing.assert_array_equal(gs, rs)
+    np.testing.assert_array_equal(gi, ri)
+    assert info["n_candidates"] == len(ri) and info["n_objects"] == P.n_polygons
+
+    w = synth.p2p_walks(n_points=10, n_lines=30_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        gs, gi = layer.candidates()
+    mbb = oracle.p2p_mbb(w.grid, Lw.verts, Lw.line_off)
+    rs, ri = oracle.cand_csr(w.grid, mbb, w.D, expand=True)
+    np.testing.assert_array_equal(gs, rs)
+    np.testing.assert_array_equal(gi, ri)
+
+
+def test_bucketing_matches_oracle_counts(api, oracle):
+    rng = np.random.default_rng(5)
+    g = synth.grid(512)
+    pts = synth.points_mixture(300_001, rng)
+    pts[:50] = [-1.0, 5.0]                 # outside the grid
+    pts[50:60] = np.nan
+    pts[60:70] = [1e5, 1.0]                # on the open edge
+    cs, perm = api.bucket_points(pts, g)
+    cs, perm = to_np(cs), to_np(perm)
+    counts = oracle.cell_counts(g, pts)
+    np.testing.assert_array_equal(cs, np.concatenate([[0], np.cumsum(counts[:-1])]))
+    n_in = cs[-1]
+    sorted_idx = perm[:n_in]
+    assert len(np.unique(sorted_idx)) == n_in
+    cells = oracle.point_cells(g, pts)
+    slot_cell = np.repeat(np.arange(len(cs) - 1), np.diff(cs))
+    np.testing.assert_array_equal(cells[sorted_idx], slot_cell)
+
+
+# ------------------------------------------------------------------ PIP
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pip_stars_full_size(api, oracle, form):
+    """1,000,000 uniform points, 1,024 star polygons, grid 256 x 256."""
+    w = synth.pip_stars()
+    ref = pip_ref(oracle, w)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        pts = torch.as_tensor(w.points, device="cuda")
+        got = to_np(api.pip_join(layer, pts, form=form))
+        st = layer.stats()
+    np.testing.assert_array_equal(got, ref)
+    assert st["hits"] == (ref >= 0).sum()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ppi", [1, 7, 32, 128])
+def test_pip_ragged_items_and_dense_cells(api, oracle, form, ppi):
+    """Few cells holding hundreds of points (several items per cell, ragged
+    tails) and polygons larger than one staging chunk (5,000 vertices)."""
+    rng = np.random.default_rng(ppi)
+    verts, sizes = [], []
+    for k, n in enumerate([5000, 300, 3]):
+        ang = np.sort(rng.uniform(0, 2 * np.pi, n))
+        r = rng.uniform(200, 450, n)
+        cx, cy = 500 + 1000 * k, 500
+        verts.append(np.stack([cx + r * np.cos(ang), cy + r * np.sin(ang)], 1))
+        sizes.append(n)
+    verts = np.concatenate(verts)
+    ring_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    pro = np.arange(len(sizes) + 1, dtype=np.int64)
+    g = dict(x0=0.0, y0=0.0, x1=4000.0, y1=1000.0, nx=8, ny=2)
+    pts = np.concatenate([rng.uniform([0, 0], [4000, 1000], (20000, 2)), rng.normal(500, 30, (3001, 2))])
+    ref = oracle.pip_join(g, pts, verts, ring_off, pro)
+    with api.pip_layer(verts, ring_off, pro, g) as layer:
+        got = to_np(api.pip_join(layer, pts, form=form, pts_per_item=ppi))
+    np.testing.assert_array_equal(got, ref)
+
+
+def layer_from_rings(polys):
+    verts, ring_off, pro = [], [0], [0]
+    for rings in polys:
+        for ring in rings:
+            verts.extend(ring)
+            ring_off.append(len(verts))
+        pro.append(len(ring_off) - 1)
+    return np.asarray(verts, np.float64).reshape(-1, 2), np.asarray(ring_off, np.int64), np.asarray(pro, np.int64)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pip_degenerate_integer_tiling(api, oracle, form):
+    """Triangles with integer corners tiling a square, queried on a half-unit
+    lattice: thousands of points on edges and vertices, FP32 y ties and zero
+    orientations -- the FP32X form must take its FP64 fallback and agree."""
+    from tests.test_oracle_pip import jittered_triangulation, dyadic_lattice
+    rng = np.random.default_rng(21)
+    polys = jittered_triangulation(rng, 10, 4, jitter=1)
+    verts, ro, pro = layer_from_rings(polys)
+    g = dict(x0=-8.0, y0=-8.0, x1=48.0, y1=48.0, nx=7, ny=7)
+    pts = dyadic_lattice(-2.0, 42.0, 0.5)
+    ref, nh = oracle.pip_join(g, pts, verts, ro, pro, with_hits=True)
+    with api.pip_layer(verts, ro, pro, g) as layer:
+        got = to_np(api.pip_join(layer, pts, form=form))
+        st = layer.stats()
+    np.testing.assert_array_equal(got, ref)
+    if form == "fp32x":
+        assert st["fallbacks"] > 0
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pip_holes_overlaps_and_translation(api, oracle, form):
+    sq = [[(0, 0), (4, 0), (4, 4), (0, 4)], [(1, 1), (1, 3), (3, 3), (3, 1)]]     # square with a hole
+    comb = [[(0, 0), (7, 0), (7, 4), (6, 4), (6, 1), (4, 1), (4, 4), (3, 4), (3, 1), (1, 1), (1, 4), (0, 4)]]
+    big = [[(-1, -1), (9, -1), (9, 9), (-1, 9)]]
+    base_polys = [sq, comb, big]
+    pts0 = np.stack(np.meshgrid(np.arange(-2, 10, 0.25), np.arange(-2, 10, 0.25)), -1).reshape(-1, 2)
+    for shift in (0.0, 65536.0, 3 * 65536.0):
+        verts, ro, pro = layer_from_rings(base_polys)
+        verts = verts + shift
+        pts = pts0 + shift
+        g = dict(x0=shift - 16, y0=shift - 16, x1=shift + 16, y1=shift + 16, nx=8, ny=8)
+        ref = oracle.pip_join(g, pts, verts, ro, pro)
+        with api.pip_layer(verts, ro, pro, g) as layer:
+            got = to_np(api.pip_join(layer, pts, form=form))
+        np.testing.assert_array_equal(got, ref)
+
+
+def test_pip_empty_and_outside(api, oracle):
+    w = synth.pip_stars(n_points=1000, n_side=4)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        out = api.pip_join(layer, np.zeros((0, 2)))
+        assert out.numel() == 0
+        pts = np.array([[-1.0, 5.0], [np.nan, 1.0], [1e5, 1e5], [2e5, 0.0]])
+        np.testing.assert_array_equal(to_np(api.pip_join(layer, pts)), -1)
+    # a layer without polygons
+    with api.pip_layer(np.zeros((0, 2)), np.zeros(1, np.int64), np.zeros(1, np.int64), w.grid) as layer:
+        np.testing.assert_array_equal(to_np(api.pip_join(layer, w.points)), -1)
+
+
+def test_layer_errors(api):
+    from paper_1403_0802_gb300._lib import SJError, SJ_ERR_INVALID, SJ_ERR_GRID_COVER
+    g = dict(x0=0.0, y0=0.0, x1=10.0, y1=10.0, nx=4, ny=4)
+    verts, ro, pro = layer_from_rings([[[(1, 1), (2, 1), (2, 2)]]])
+    with pytest.raises(SJError) as e:
+        api.pip_layer(verts + 20.0, ro, pro, g)
+    assert e.value.status == SJ_ERR_GRID_COVER
+    with pytest.raises(SJError) as e:
+        api.pip_layer(verts[:2], np.array([0, 2]), pro, g)            # ring of two vertices
+    assert e.value.status == SJ_ERR_INVALID
+    bad = verts.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(SJError) as e:
+        api.pip_layer(bad, ro, pro, g)
+    assert e.value.status == SJ_ERR_INVALID
+    with pytest.raises(SJError) as e:
+        api.p2p_layer(verts, np.array([0, 3]), -1.0, g)
+    assert e.value.status == SJ_ERR_INVALID
+
+
+# ------------------------------------------------------------------ P2P
+
+@pytest.mark.parametrize("form", FORMS)
+def test_p2p_walks_full_size(api, oracle, form):
+    """10,000,000 mixture points, 100,000 random-walk polylines, D = 100 m,
+    grid 1024 x 1024 -- the benchmark's workload and launch configuration."""
+    w = synth.p2p_walks()
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        pts = torch.as_tensor(w.points, device="cuda")
+        gid, gd = api.p2p_join(layer, pts, form=form)
+        gid, gd = to_np(gid), to_np(gd)
+    r = check_p2p(oracle, w, gid, gd, form)
+    assert 0.5 < r["hit_frac"] < 0.99
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("ppi", [1, 13, 64, 128])
+def test_p2p_subset_ragged_items(api, oracle, form, ppi):
+    w = synth.p2p_walks(n_points=200_003, n_lines=20_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        gid, gd = api.p2p_join(layer, w.points, form=form, pts_per_item=ppi)
+    check_p2p(oracle, w, to_np(gid), to_np(gd), form)
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_p2p_degenerate_polylines(api, oracle, form):
+    """One-vertex polylines, zero-length segments, duplicated polylines (exact
+    ties go to the smaller id), points on polylines and at exactly D, long
+    polylines spanning several staging chunks."""
+    rng = np.random.default_rng(3)
+    lines = [
+        [(100.0, 100.0)],                                  # a point
+        [(200.0, 200.0), (200.0, 200.0), (260.0, 200.0)],  # zero-length first segment
+        [(300.0, 300.0), (340.0, 300.0)],
+        [(300.0, 300.0), (340.0, 300.0)],                  # duplicate of the previous one
+        [(500.0, 500.0), (500.0, 600.0), (600.0, 600.0)],
+    ]
+    t = np.linspace(0, 2 * np.pi, 600)
+    lines.append(list(zip(700 + 150 * np.cos(t), 700 + 150 * np.sin(t))))   # 600 vertices, > 1 chunk
+    verts = np.concatenate([np.asarray(l, np.float64) for l in lines])
+    off = np.concatenate([[0], np.cumsum([len(l) for l in lines])]).astype(np.int64)
+    D = 16.0
+    pts = np.concatenate([
+        np.array([[100.0, 116.0], [100.0, 116.0001], [230.0, 216.0], [320.0, 310.0], [320.0, 300.0],
+                  [500.0, 550.0], [550.0, 600.0], [100.0, 100.0], [700.0, 700.0], [850.0, 700.0]]),
+        rng.uniform(0, 1024, (50000, 2))])
+    g = dict(x0=0.0, y0=0.0, x1=1024.0, y1=1024.0, nx=32, ny=32)
+
+    class W:
+        pass
+    w = W()
+    w.grid, w.points, w.D, w.polylines = g, pts, D, None
+    with api.p2p_layer(verts, off, D, g) as layer:
+        gid, gd = api.p2p_join(layer, pts, form=form)
+    gid, gd = to_np(gid), to_np(gd)
+    check_p2p(oracle, w, gid, gd, form, verts=verts, line_off=off)
+    assert gid[0] == 0 and gd[0] == 16.0                # exactly D: inclusive window
+    assert gid[1] == -1
+    assert gid[3] == 2                                   # tie between ids 2 and 3
+    assert gid[4] == 2 and gd[4] == 0.0
+    assert gid[7] == 0 and gd[7] == 0.0
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_host_buffers_match_device(api, oracle, form):
+    w = synth.p2p_walks(n_points=50_000, n_lines=10_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        did, dd = api.p2p_join(layer, w.points, form=form)
+        hid, hd = api.p2p_join_host(layer, w.points, form=form)
+    np.testing.assert_array_equal(to_np(did), hid)
+    np.testing.assert_array_equal(to_np(dd), hd)
+    w = synth.pip_stars(n_points=50_000)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        np.testing.assert_array_equal(to_np(api.pip_join(layer, w.points, form=form)),
+                                      api.pip_join_host(layer, w.points, form=form))
+
+
+def test_fp32x_fallback_rate_is_small(api, oracle):
+    w = synth.p2p_walks(n_points=1_000_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        api.p2p_join(layer, w.points, form="fp32x")
+        st = layer.stats()
+    assert st["fallbacks"] < 1e-3 * st["points"]
