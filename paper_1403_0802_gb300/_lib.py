@@ -36,6 +36,12 @@ class sj_run_stats(C.Structure):
                 ("refine_launches", C.c_int64), ("refine_ms", C.c_double)]
 
 
+class sj_peak_rates(C.Structure):
+    _fields_ = [("sms", C.c_int32), ("pad", C.c_int32), ("ffma_per_s", C.c_double), ("ffma_per_clk_sm", C.c_double),
+                ("fadd_per_s", C.c_double), ("fadd_per_clk_sm", C.c_double), ("dfma_per_s", C.c_double),
+                ("dfma_per_clk_sm", C.c_double), ("dadd_per_s", C.c_double), ("dadd_per_clk_sm", C.c_double)]
+
+
 SJ_OK, SJ_ERR_INVALID, SJ_ERR_OOM, SJ_ERR_GRID_COVER, SJ_ERR_CUDA, SJ_ERR_TIMEOUT, SJ_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
 SJ_FP64, SJ_FP32X = 0, 1
 SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
@@ -59,6 +65,7 @@ SIGNATURES = {
     "sj_layer_reset_stats": (C.c_int, [_P]),
     "sj_last_error": (C.c_char_p, []),
     "sj_version": (C.c_char_p, []),
+    "sj_peaks_measure": (C.c_int, [C.POINTER(sj_peak_rates)]),
 }
 
 

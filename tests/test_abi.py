@@ -8,13 +8,16 @@ import re
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "sj.h")
+INCLUDE = os.path.join(ROOT, "include")
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sj_[a-z0-9_]+)\s*\(", text)))
+    names = set()
+    for f in sorted(os.listdir(INCLUDE)):
+        if f.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(sj_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -67,3 +70,12 @@ def test_struct_layouts_match_header():
     assert C.sizeof(_lib.sj_opts) == 24
     assert C.sizeof(_lib.sj_run_stats) == 72
     assert C.sizeof(_lib.sj_layer_info) == 48
+
+
+def test_binding_imports_without_a_gpu():
+    """The Python front end imports on a CPU-only host (the library is only
+    loaded, never called)."""
+    from paper_1403_0802_gb300 import api, synth  # noqa: F401
+    assert api.FORMS == {"fp64": 0, "fp32x": 1}
+    o = api._opts("fp32x", "persistent", 32, True)
+    assert (o.form, o.launch, o.pts_per_item, o.flags) == (1, 1, 32, 1)
