@@ -192,6 +192,30 @@ sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32
 sj_status sj_layer_get_stats(const sj_layer *layer, sj_run_stats *out);
 sj_status sj_layer_reset_stats(sj_layer *layer);
 
+/* P2P join that allocates nothing.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory when they join
+ * -- code on a hard latency budget (an allocation can stall), code living in
+ * a pre-sized memory arena, or hosts whose allocator is owned by another
+ * component.  It computes exactly what sj_p2p_join computes (same kernels,
+ * same results), but every byte of scratch comes from one fixed device array
+ * built into the library (about 32 MB, held on every GPU that loads the
+ * library until the process exits).  The caller still passes the points and
+ * the outputs (same layout and meaning as sj_p2p_join).
+ *   N <= SJ_NOALLOC_MAX_POINTS and the layer's grid <= SJ_NOALLOC_MAX_CELLS
+ *   cells, else SJ_ERR_INVALID with a message; pts_per_item and flags in opts
+ *   are ignored (64 points per item, no timing events).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the previous call's
+ * contents (the counters that must start at zero are cleared on `stream` at
+ * the start of each call): calls whose kernels overlap on the GPU race, so
+ * issue them on one stream or order them with events.  Asynchronous on
+ * stream. */
+#define SJ_NOALLOC_MAX_POINTS 524288
+#define SJ_NOALLOC_MAX_CELLS 1048576
+sj_status sj_p2p_join_noalloc(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
+                              const sj_opts *opts, void *stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sj_last_error(void);
 

@@ -158,6 +158,21 @@ def p2p_join(layer: Layer, pts, out_id: torch.Tensor | None = None, out_d: torch
     return out_id, out_d
 
 
+def p2p_join_noalloc(layer: Layer, pts, out_id: torch.Tensor, out_d: torch.Tensor | None = None,
+                     form: str = "fp64", stream=None):
+    """p2p_join for callers that must not allocate device memory: the caller
+    supplies the outputs and the library takes its scratch from a fixed
+    built-in device array (at most 524,288 points and 1,048,576 grid cells per
+    call; calls must not overlap on the GPU).  Nothing here allocates either:
+    the points must already be a float64 [N, 2] CUDA tensor."""
+    if not (isinstance(pts, torch.Tensor) and pts.is_cuda and pts.dtype == torch.float64 and pts.is_contiguous()):
+        raise ValueError("points must be a contiguous float64 [N, 2] CUDA tensor")
+    o = _opts(form)
+    L.check(L.lib().sj_p2p_join_noalloc(layer.handle, _ptr(pts), pts.shape[0], _ptr(out_id), _ptr(out_d), C.byref(o),
+                                        _stream(stream)), "sj_p2p_join_noalloc")
+    return out_id, out_d
+
+
 def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, form: str = "fp64",
                   stream=None) -> np.ndarray:
     """Same as pip_join from host memory (copies in and out; synchronous)."""

@@ -663,3 +663,135 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
 extern "C" const char *sj_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char *sj_version(void) { return "sj 0.1 (sm_103a)"; }
+
+// ------------------------------------------------------------------ P2P join without allocation
+//
+// Some callers cannot allocate device memory at the moment they join: code on
+// a hard latency budget (a device allocation can stall for milliseconds),
+// code that runs inside a pre-sized memory arena or a fixed memory budget, and
+// hosts where another component owns the CUDA allocator and forbids
+// allocations from libraries.  sj_p2p_join_noalloc runs the same kernels as
+// sj_p2p_join but takes all of its scratch from one file-scope device array
+// of fixed size, so it calls no allocator at all.
+//
+// The array is part of this module's device image: every GPU that loads the
+// module holds it until the process exits.  All calls share it, so two calls
+// whose kernels overlap on the GPU race on it; callers must serialise them
+// (one stream, or events between streams).  It keeps the previous call's
+// contents, so the counters that must start at zero are cleared on the
+// caller's stream at the start of every call.
+
+namespace {
+
+constexpr int64_t NOALLOC_MAX_POINTS = SJ_NOALLOC_MAX_POINTS;
+constexpr int64_t NOALLOC_MAX_CELLS = SJ_NOALLOC_MAX_CELLS;
+constexpr int NOALLOC_CH = 64;
+constexpr size_t NOALLOC_BYTES = 32u << 20;   // holds carve() at the two limits above (about 31.6 MB)
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+void *g_noalloc_ptr[64];
+std::mutex g_noalloc_mu;
+
+// Device address of the array on the current device, looked up once per
+// device (host code cannot use the symbol itself: on the host it names a
+// stand-in, not device memory).
+sj_status noalloc_scratch(int dev, char **out) {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(noalloc scratch)");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (char *)g_noalloc_ptr[dev];
+    return SJ_OK;
+}
+
+}  // namespace
+
+extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id,
+                                         double *out_d, const sj_opts *o, void *stream) {
+    if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
+    if (L->kind != KIND_P2P) return fail(SJ_ERR_INVALID, "not a polyline layer");
+    if (N < 0 || N > NOALLOC_MAX_POINTS)
+        return fail(SJ_ERR_INVALID, "sj_p2p_join_noalloc: N must be in 0.." + std::to_string(NOALLOC_MAX_POINTS) +
+                                        " (fixed scratch size); use sj_p2p_join for larger batches");
+    if ((int64_t)L->g.G > NOALLOC_MAX_CELLS)
+        return fail(SJ_ERR_INVALID, "sj_p2p_join_noalloc: the layer's grid has more than " +
+                                        std::to_string(NOALLOC_MAX_CELLS) + " cells (fixed scratch size)");
+    if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
+    if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
+    const int form = o ? o->form : SJ_FP64;
+    if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != L->device) return fail(SJ_ERR_INVALID, "layer belongs to another device");
+    if (dev < 0 || dev >= 64) return fail(SJ_ERR_INVALID, "device index out of range");
+    DevInfo *di;
+    sj_status st = device_info(dev, &di);
+    if (st != SJ_OK) return st;
+    char *base = nullptr;
+    st = noalloc_scratch(dev, &base);
+    if (st != SJ_OK) return st;
+    if (N == 0) return SJ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int G = L->g.G;
+    const bool need_fb = form == SJ_FP32X;
+    JoinBufs b;
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, NOALLOC_CH, need_fb); });
+    if (bytes > NOALLOC_BYTES) return fail(SJ_ERR_INVALID, "sj_p2p_join_noalloc: scratch does not fit");
+    Scratch sc;
+    sc.base = base;
+    carve(sc, b, N, G, NOALLOC_CH, need_fb);
+    CUDA_TRY(cudaMemsetAsync(b.cnt, 0, sizeof(int) * ((size_t)G + 1), s));
+    CUDA_TRY(cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s));
+
+    BucketArgs ba{};
+    ba.g = L->g;
+    ba.pts = (const double2 *)pts;
+    ba.n = (int)N;
+    ba.cnt = b.cnt;
+    ba.key_rank = b.key_rank;
+    ba.cell_start = b.cell_start;
+    ba.perm = b.perm;
+    ba.spts = b.spts;
+    ba.cand_start = L->cand_start;
+    ba.ch = NOALLOC_CH;
+    ba.items = b.items;
+    ba.block_sums = b.block_sums;
+    ba.totals = b.totals;
+    ba.out_id = out_id;
+    ba.out_d = out_d;
+    CUDA_TRY(launch_bucket(ba, s));
+
+    RefineArgs ra{};
+    ra.g = L->g;
+    ra.items = b.items;
+    ra.n_items = b.totals + 1;
+    ra.cell_start = b.cell_start;
+    ra.perm = b.perm;
+    ra.spts = b.spts;
+    ra.cand_start = L->cand_start;
+    ra.cand_ids = L->cand_ids;
+    ra.obj_voff = L->obj_voff;
+    ra.verts = L->verts;
+    ra.vsplit = L->vsplit;
+    ra.seg_e64 = L->seg_e64;
+    ra.seg_inv64 = L->seg_inv64;
+    ra.seg_e32 = L->seg_e32;
+    ra.seg_inv32 = L->seg_inv32;
+    ra.D = L->D;
+    ra.eps_abs = L->eps_abs;
+    ra.ch = NOALLOC_CH;
+    ra.out_id = out_id;
+    ra.out_d = out_d;
+    ra.fb = b.fb;
+    ra.n_fb = b.totals + 2;
+    ra.stats = L->stats;
+    CUDA_TRY(launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s));
+    if (need_fb) CUDA_TRY(launch_p2p_recheck(ra, di->sms * 4, s));
+    L->joins++;
+    L->points += N;
+    return SJ_OK;
+}
