@@ -47,7 +47,7 @@ extern "C" {
 #endif
 
 /* Uniform grid over [x0, x1) x [y0, y1) with nx * ny cells (Sec. III.A).
- * Requires x1 > x0, y1 > y0, nx, ny >= 1 and nx * ny < 2^31 - 1. */
+ * Requires finite x0 < x1, y0 < y1, 1 <= nx, ny <= 2^20 and nx * ny < 2^31 - 1. */
 typedef struct {
     double x0, y0, x1, y1;
     int32_t nx, ny;

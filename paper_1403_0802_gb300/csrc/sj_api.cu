@@ -27,6 +27,7 @@ cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, doubl
 cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s);
 cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s);
+cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 int pip_blocks_per_sm(int form);
 int p2p_blocks_per_sm(int form);
 }  // namespace sj
@@ -58,6 +59,7 @@ struct sj_layer {
     int *cand_start = nullptr;
     int *cand_ids = nullptr;
     unsigned long long *stats = nullptr;
+    unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     mutable std::atomic<long long> joins{0};
     mutable std::atomic<long long> points{0};
     // SJ_FLAG_TIME_REFINE: event pairs recorded around refinement launches,
@@ -124,6 +126,7 @@ static sj_status device_info(int dev, DevInfo **out) {
 static bool grid_ok(const sj_grid *g) {
     if (!g) return false;
     if (!(g->nx >= 1 && g->ny >= 1)) return false;
+    if (g->nx > (1 << 20) || g->ny > (1 << 20)) return false;
     if ((int64_t)g->nx * (int64_t)g->ny > 2147483646LL) return false;
     if (!(std::isfinite(g->x0) && std::isfinite(g->x1) && std::isfinite(g->y0) && std::isfinite(g->y1))) return false;
     return g->x1 > g->x0 && g->y1 > g->y0;
@@ -137,7 +140,20 @@ static GridDev make_grid(const sj_grid *g) {
     volatile double cw = (g->x1 - g->x0) / (double)g->nx;   // one IEEE division each
     volatile double ch = (g->y1 - g->y0) / (double)g->ny;
     d.cw = cw; d.ch = ch;
+    d.x0f = (float)g->x0; d.y0f = (float)g->y0;
+    d.icwf = (float)(1.0 / cw); d.ichf = (float)(1.0 / ch);
+    d.kx = d.ky = nullptr;
     return d;
+}
+
+// Threshold tables of point_cell for the grid of layer L (computed on the GPU
+// with the FP64 cell rule itself).
+static sj_status layer_tables(sj_layer *L, cudaStream_t s) {
+    CUDA_TRY(cudaMalloc((void **)&L->cell_keys, sizeof(unsigned long long) * ((size_t)L->g.nx + L->g.ny + 2)));
+    CUDA_TRY(launch_thresholds(L->g, L->cell_keys, L->cell_keys + L->g.nx + 1, s));
+    L->g.kx = L->cell_keys;
+    L->g.ky = L->cell_keys + L->g.nx + 1;
+    return SJ_OK;
 }
 
 static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
@@ -182,7 +198,7 @@ static void resolve_events(const sj_layer *L) {
 static void layer_free(sj_layer *L) {
     resolve_events(L);
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
-                    L->seg_inv64, L->seg_e32, L->seg_inv32, L->mbb, L->cand_start, L->cand_ids, L->stats};
+                    L->seg_inv64, L->seg_e32, L->seg_inv32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -306,6 +322,10 @@ extern "C" sj_status sj_pip_layer_create(const double *verts, int64_t V, const i
     CUDA_TRY(cudaGetDevice(&L->device));
     L->grid = *g;
     L->g = make_grid(g);
+    {
+        sj_status ts = layer_tables(L, s);
+        if (ts != SJ_OK) return ts;
+    }
     L->nobj = P;
     L->V = (int)V;
     L->R = R;
@@ -355,6 +375,10 @@ extern "C" sj_status sj_p2p_layer_create(const double *verts, int64_t V, const i
     CUDA_TRY(cudaGetDevice(&L->device));
     L->grid = *g;
     L->g = make_grid(g);
+    {
+        sj_status ts = layer_tables(L, s);
+        if (ts != SJ_OK) return ts;
+    }
     L->nobj = Lc;
     L->V = (int)V;
     L->R = Lc;
@@ -630,17 +654,21 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
     cudaStream_t s = (cudaStream_t)stream;
     GridDev gd = make_grid(g);
     Scratch sc;
-    auto lay = [&](Scratch &x, int **cnt, int **totals, int2 **kr, int2 **bs) {
+    auto lay = [&](Scratch &x, int **cnt, int **totals, int2 **kr, int2 **bs, unsigned long long **keys) {
         *cnt = x.take<int>((size_t)gd.G + 1);
         *totals = x.take<int>(4);
         *kr = x.take<int2>((size_t)N);
         *bs = x.take<int2>(bucket_scan_blocks(gd.G));
+        *keys = x.take<unsigned long long>((size_t)gd.nx + gd.ny + 2);
     };
     int *cnt, *totals;
     int2 *kr, *bs;
-    size_t bytes = measure([&](Scratch &x) { lay(x, &cnt, &totals, &kr, &bs); });
+    unsigned long long *keys;
+    size_t bytes = measure([&](Scratch &x) { lay(x, &cnt, &totals, &kr, &bs, &keys); });
     CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
-    lay(sc, &cnt, &totals, &kr, &bs);
+    lay(sc, &cnt, &totals, &kr, &bs, &keys);
+    gd.kx = keys;
+    gd.ky = keys + gd.nx + 1;
     BucketArgs ba{};
     ba.g = gd;
     ba.pts = (const double2 *)pts;
@@ -653,6 +681,7 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
     ba.totals = totals;
     ba.ch = 1;
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)gd.G + 1), s);
+    if (e == cudaSuccess) e = launch_thresholds(gd, keys, keys + gd.nx + 1, s);
     if (e == cudaSuccess) e = launch_bucket(ba, s);
     cudaError_t e2 = cudaFreeAsync(sc.base, s);
     if (e != cudaSuccess) return cuda_fail(e, "bucket launch");

@@ -131,6 +131,29 @@ struct OffsetApply {
     }
 };
 
+// ------------------------------------------------------------------ cell threshold tables
+
+// keys[k] = order key of the smallest double v with floor(fl(fl(v - lo) / w)) >= k,
+// k = 0..n, by binary search over the order keys of [-inf, +inf] (the rule is
+// monotone in v, false at -inf and true at +inf).  64 steps per threshold.
+__global__ void k_axis_thresholds(double lo, double w, int n, unsigned long long *keys) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > n) return;
+    const double INF = __longlong_as_double(0x7ff0000000000000LL);
+    unsigned long long a = order_key(-INF), b = order_key(INF);
+    while (b - a > 1) {
+        const unsigned long long m = a + (b - a) / 2;
+        if (axis_floor(key_value(m), lo, w) >= (double)k) b = m; else a = m;
+    }
+    keys[k] = b;
+}
+
+cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s) {
+    k_axis_thresholds<<<(g.nx + 1 + 127) / 128, 128, 0, s>>>(g.x0, g.cw, g.nx, kx);
+    k_axis_thresholds<<<(g.ny + 1 + 127) / 128, 128, 0, s>>>(g.y0, g.ch, g.ny, ky);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ point bucketing
 
 // a1: cell id per point and per-cell count; the atomic's return value is the

@@ -13,11 +13,15 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_CH = 128;        // largest point chunk per work item
 constexpr float U32 = 5.9604644775390625e-08f;   // 2^-24, unit roundoff of FP32
 
-// Grid with derived cell sizes (computed once on the host, FP64, rounded).
+// Grid with derived cell sizes (computed once on the host, FP64, rounded) and
+// the per-axis threshold tables of point_cell.
 struct GridDev {
     double x0, y0, x1, y1;
     double cw, ch;     // (x1 - x0) / nx, (y1 - y0) / ny
     int nx, ny, G;
+    const unsigned long long *kx;   // [nx + 1] order keys of the x thresholds
+    const unsigned long long *ky;   // [ny + 1]
+    float x0f, y0f, icwf, ichf;     // FP32 estimates of x0, y0, 1 / cw, 1 / ch
 };
 
 // Cell of one coordinate: floor((v - lo) / w) as a double (may be out of range
@@ -26,14 +30,54 @@ __device__ __forceinline__ double axis_floor(double v, double lo, double w) {
     return floor(__ddiv_rn(__dsub_rn(v, lo), w));
 }
 
+// Order-preserving map of a double to an unsigned 64-bit key (x < y iff
+// key(x) < key(y) for non-NaN values; -0 sorts just below +0).
+__device__ __forceinline__ unsigned long long order_key(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ULL);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+    return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffULL) : ~k));
+}
+
+// FP32 value of a finite double, truncated, from its bit pattern with integer
+// operations only (no FP64 instruction); magnitudes outside the FP32 normal
+// range are clamped.  Only used as an estimate.
+__device__ __forceinline__ float approx_float(double v) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    unsigned hi = (unsigned)(b >> 32);
+    int e = (int)((hi >> 20) & 0x7ff) - 896;          // FP32 biased exponent
+    unsigned m = (unsigned)(b >> 29) & 0x7fffffu;
+    unsigned bits = (e <= 0) ? 0u : (e >= 255 ? 0x7f7fffffu : (((unsigned)e << 23) | m));
+    return __uint_as_float(bits | (hi & 0x80000000u));
+}
+
+// Cell index along one axis by threshold table: keys[k] is the order key of the
+// smallest double whose cell, floor(fl(fl(v - lo) / w)), is >= k, so the cell
+// of v is the k with keys[k] <= key(v) < keys[k + 1] (exactly the FP64 rule:
+// the rule is monotone in v).  An FP32 estimate picks the start; integer key
+// compares walk to the exact cell.  Returns -1 outside [keys[0], keys[n]).
+__device__ __forceinline__ int axis_cell(double v, const unsigned long long *keys, int n, float lof, float iwf) {
+    const unsigned long long k = order_key(v);
+    if (k < keys[0] || k >= keys[n]) return -1;
+    float t = floorf((approx_float(v) - lof) * iwf);
+    int i = (t >= (float)(n - 1)) ? n - 1 : (t > 0.0f ? (int)t : 0);
+    while (k < keys[i]) --i;          // keys[0] <= k, so this stops at i >= 0
+    while (k >= keys[i + 1]) ++i;     // k < keys[n], so this stops at i <= n - 1
+    return i;
+}
+
 // Cell id of a point (Sec. III.A), G when it lies outside the half-open grid
-// box or has a NaN coordinate.  ix is in range iff 0 <= floor(t) < n, which is
-// the same as 0 <= t < n for the rounded quotient t.
+// box or has a NaN or infinite coordinate.
 __device__ __forceinline__ int point_cell(const GridDev &g, double x, double y) {
-    double fx = axis_floor(x, g.x0, g.cw);
-    double fy = axis_floor(y, g.y0, g.ch);
-    if (!(fx >= 0.0 && fx < (double)g.nx && fy >= 0.0 && fy < (double)g.ny)) return g.G;
-    return (int)fy * g.nx + (int)fx;
+    const unsigned long long EXP = 0x7ff0000000000000ULL;
+    if (((unsigned long long)__double_as_longlong(x) & EXP) == EXP ||
+        ((unsigned long long)__double_as_longlong(y) & EXP) == EXP)
+        return g.G;
+    const int ix = axis_cell(x, g.kx, g.nx, g.x0f, g.icwf);
+    const int iy = axis_cell(y, g.ky, g.ny, g.y0f, g.ichf);
+    if (ix < 0 || iy < 0) return g.G;
+    return iy * g.nx + ix;
 }
 
 // floor((v - lo) / w) clamped to [0, n - 1] (rasterisation of MBB corners).

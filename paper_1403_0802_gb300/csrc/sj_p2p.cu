@@ -2,14 +2,18 @@
 // item, the candidate polyline at the smallest distance, accepted when the
 // distance is within the window D.
 //
-// Work decomposition: one warp per (cell, point-chunk) item.  For each
-// candidate polyline, in id order, the warp stages its segments in shared
-// memory (start point a, direction e = b - a, 1 / |e|^2) and splits its lanes
-// into point groups of SG lanes; a group's lanes stride over the segments,
-// keep a running minimum of the squared distance, and fold it with SG-lane
-// shuffles (the cross-lane min of the paper's vertex-per-lane alternative,
-// Sec. III.B).  Per point the warp keeps the best (distance, id) and the
-// second-best distance of another polyline in shared memory.
+// Work decomposition: one warp per (cell, point-chunk) item.  The warp first
+// reads the metadata of up to 32 candidate polylines at once (one per lane),
+// warp-scans their segment counts, and stages the concatenated segments of
+// all of them in shared memory in one strided pass (start point a, direction
+// e = b - a, 1 / |e|^2, polyline id) -- so the L2 round trips of different
+// candidates overlap instead of forming a chain per candidate.  It then splits
+// its lanes into point groups of SG lanes (SG chosen so that np points x S
+// segments fill the warp); each lane strides over the segments keeping a
+// running "top-2" -- the best (squared distance, polyline) and the best
+// distance of any *other* polyline -- and the SG lanes of a group fold their
+// top-2s with shuffles (the cross-lane min of the vertex-per-lane alternative
+// of Sec. III.B).  Per point the result lives in shared memory across chunks.
 //
 // The point-to-segment distance is the two-case distance of Fig. 2 written as
 // the clamped projection: t = clamp(((p - a) . e) / |e|^2, 0, 1) and
@@ -17,14 +21,16 @@
 // perpendicular foot; a zero-length segment has 1 / |e|^2 = 0, hence t = 0).
 //
 // Two arithmetic forms:
-//   FP64   -- the formula in FP64; agrees with the two-case FP64 evaluation to
-//             a few ulps of the coordinates' magnitude.
+//   FP64   -- the formula in FP64 (ties of equal squared distance go to the
+//             smaller id); agrees with the two-case FP64 evaluation to a few
+//             ulps of the coordinates' magnitude.
 //   FP32X  -- cell-relative FP32 coordinates; every (point, polyline) distance
-//             carries a bound E = 64 u max|coordinate| + 4 eps.  A point is
-//             final only when its best polyline is separated from the runner-up
-//             by more than the two bounds and its distance from D by more than
-//             its bound; otherwise it is queued and redone in FP64
-//             (k_p2p_recheck).
+//             carries the bound E = 64 u max|coordinate| + 4 eps (u = 2^-24,
+//             max over the point and every staged vertex of the item).  A
+//             point is final only when its best polyline is ahead of the
+//             runner-up by more than 2E and its distance differs from D by
+//             more than E; otherwise it is queued and redone in FP64
+//             (k_p2p_recheck), so ids agree with FP64 up to exact ties.
 #include <cuda_runtime.h>
 
 #include <type_traits>
@@ -34,23 +40,27 @@
 namespace sj {
 
 constexpr int P2P_WARPS = 4;
-constexpr int SMAX32 = 256, SMAX64 = 128;
 
 template <bool FP32>
-struct P2PSmem;
-
+struct P2PCfg {
+    using T = float;
+    static constexpr int SMAX = 512;   // staged segments per chunk per warp
+};
 template <>
-struct P2PSmem<true> {
-    float ax[SMAX32], ay[SMAX32], ex[SMAX32], ey[SMAX32], inv[SMAX32];
-    float px[MAX_CH], py[MAX_CH], cur[MAX_CH], d1[MAX_CH], d2[MAX_CH], e1[MAX_CH], e2[MAX_CH];
-    int id1[MAX_CH];
+struct P2PCfg<false> {
+    using T = double;
+    static constexpr int SMAX = 256;
 };
 
-template <>
-struct P2PSmem<false> {
-    double ax[SMAX64], ay[SMAX64], ex[SMAX64], ey[SMAX64], inv[SMAX64];
-    double px[MAX_CH], py[MAX_CH], cur[MAX_CH], d1[MAX_CH];
-    int id1[MAX_CH];
+template <bool FP32>
+struct P2PSmem {
+    using T = typename P2PCfg<FP32>::T;
+    static constexpr int SMAX = P2PCfg<FP32>::SMAX;
+    T ax[SMAX], ay[SMAX], ex[SMAX], ey[SMAX], inv[SMAX];
+    int sid[SMAX];
+    int coff[33], cid[32], cvb[32];   // candidate group: segment offsets, ids, first vertices
+    T px[MAX_CH], py[MAX_CH], b1[MAX_CH], b2[MAX_CH];
+    int i1[MAX_CH];
 };
 
 // Squared distance from p to the segment (a, a + e) by the clamped projection.
@@ -70,24 +80,70 @@ __device__ __forceinline__ double seg_d2(double px, double py, double ax, double
     return __fma_rn(qx, qx, __dmul_rn(qy, qy));
 }
 
+// Running result of one point over a set of segments: b1 = smallest squared
+// distance, i1 = its polyline, b2 = smallest squared distance of any segment of
+// another polyline (FP32X certificate; unused in FP64).
 template <typename T>
-__device__ __forceinline__ T tmin(T a, T b);
-template <>
-__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
-template <>
-__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
+struct Best {
+    T b1, b2;
+    int i1;
+};
+
+template <bool FP32, typename T>
+__device__ __forceinline__ void consider(Best<T> &s, T d, int l) {
+    if constexpr (FP32) {
+        if (d < s.b1) {
+            s.b2 = (l != s.i1) ? s.b1 : s.b2;
+            s.b1 = d;
+            s.i1 = l;
+        } else if (d < s.b2 && l != s.i1) {
+            s.b2 = d;
+        }
+    } else {
+        if (d < s.b1 || (d == s.b1 && l < s.i1)) {
+            s.b1 = d;
+            s.i1 = l;
+        }
+    }
+}
+
+// Result over the union of two segment sets (commutative and associative).
+template <bool FP32, typename T>
+__device__ __forceinline__ Best<T> merge(Best<T> A, Best<T> B) {
+    Best<T> r;
+    if constexpr (FP32) {
+        if (A.i1 == B.i1) {
+            r.b1 = fminf(A.b1, B.b1); r.i1 = A.i1; r.b2 = fminf(A.b2, B.b2);
+        } else if (B.b1 < A.b1 || (B.b1 == A.b1 && B.i1 < A.i1)) {
+            r.b1 = B.b1; r.i1 = B.i1; r.b2 = fminf(B.b2, A.b1);
+        } else {
+            r.b1 = A.b1; r.i1 = A.i1; r.b2 = fminf(A.b2, B.b1);
+        }
+    } else {
+        r = (B.b1 < A.b1 || (B.b1 == A.b1 && B.i1 < A.i1)) ? B : A;
+    }
+    return r;
+}
+
+template <bool FP32, typename T>
+__device__ __forceinline__ Best<T> shfl_best(const Best<T> &s, int o) {
+    Best<T> r;
+    r.b1 = __shfl_xor_sync(FULL, s.b1, o);
+    r.i1 = __shfl_xor_sync(FULL, s.i1, o);
+    r.b2 = FP32 ? __shfl_xor_sync(FULL, s.b2, o) : s.b2;
+    return r;
+}
 
 template <bool FP32>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
-    using T = typename std::conditional<FP32, float, double>::type;
-    constexpr int SMAX = FP32 ? SMAX32 : SMAX64;
-    __shared__ P2PSmem<FP32> smem[P2P_WARPS];
+    using T = typename P2PCfg<FP32>::T;
+    constexpr int SMAX = P2PCfg<FP32>::SMAX;
+    extern __shared__ __align__(16) unsigned char p2p_smem_raw[];
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    P2PSmem<FP32> &s = smem[w];
+    P2PSmem<FP32> &s = reinterpret_cast<P2PSmem<FP32> *>(p2p_smem_raw)[w];
     const int n_items = *a.n_items;
     const T INF = (T)__longlong_as_double(0x7ff0000000000000LL);
-    unsigned long long c_pairs = 0, c_tests = 0;
-    unsigned long long c_items = 0;
+    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0;
     unsigned c_fb = 0, c_hits = 0;
 
     for (int it = blockIdx.x * P2P_WARPS + w; it < n_items; it += gridDim.x * P2P_WARPS) {
@@ -96,6 +152,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         const int c = item.x;
         const int j0 = a.cell_start[c] + item.y;
         const int np = min(a.ch, a.cell_start[c + 1] - j0);
+        const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
         double2 fr = make_double2(0.0, 0.0);
         if (FP32) fr = cell_frame(a.g, c);
         const float fox = (float)fr.x, foy = (float)fr.y;
@@ -105,31 +162,55 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             if constexpr (FP32) {
                 s.px[q] = __double2float_rn(__dsub_rn(p.x, fr.x));
                 s.py[q] = __double2float_rn(__dsub_rn(p.y, fr.y));
-                s.d2[q] = INF;
-                s.e1[q] = 0.0f;
-                s.e2[q] = 0.0f;
             } else {
                 s.px[q] = p.x;
                 s.py[q] = p.y;
             }
-            s.cur[q] = INF;
-            s.d1[q] = INF;
-            s.id1[q] = -1;
+            s.b1[q] = INF;
+            s.b2[q] = INF;
+            s.i1[q] = -1;
         }
-        __syncwarp();
+        float mag = 0.0f;   // FP32X: largest |cell-relative coordinate| staged for this item
+        c_pairs += (unsigned long long)np * (unsigned long long)(k1 - k0);
 
-        const int k1 = a.cand_start[c + 1];
-        for (int k = a.cand_start[c]; k < k1; ++k) {
-            const int lid = a.cand_ids[k];
-            const int vb = a.obj_voff[lid], nv = a.obj_voff[lid + 1] - vb;
-            const int nseg = nv > 1 ? nv - 1 : 1;
-            c_pairs += np;
-            c_tests += (unsigned long long)np * (unsigned long long)nseg;
-            float mag = 0.0f;   // FP32X: largest |cell-relative coordinate| of the polyline
-            for (int s0 = 0; s0 < nseg; s0 += SMAX) {
-                const int ns = min(SMAX, nseg - s0);
+        for (int kg = k0; kg < k1; kg += 32) {
+            // candidate group: one polyline per lane, segment counts scanned
+            const int nc = min(32, k1 - kg);
+            int lid = 0, vb = 0, nseg = 0;
+            if (lane < nc) {
+                lid = a.cand_ids[kg + lane];
+                vb = a.obj_voff[lid];
+                const int nv = a.obj_voff[lid + 1] - vb;
+                nseg = nv > 1 ? nv - 1 : 1;
+            }
+            int incl = nseg;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int S = __shfl_sync(FULL, incl, 31);
+            __syncwarp();   // previous chunk's readers are done with the staging area
+            if (lane < nc) {
+                s.coff[lane] = incl - nseg;
+                s.cid[lane] = lid;
+                s.cvb[lane] = vb;
+            }
+            if (lane == 0) s.coff[nc] = S;
+            __syncwarp();
+            c_tests += (unsigned long long)np * (unsigned long long)S;
+
+            for (int s0 = 0; s0 < S; s0 += SMAX) {
+                const int ns = min(SMAX, S - s0);
                 for (int t = lane; t < ns; t += 32) {
-                    const int i = vb + s0 + t;
+                    const int g = s0 + t;
+                    int lo = 0, hi = nc;   // coff[lo] <= g < coff[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s.coff[mid] <= g) lo = mid; else hi = mid;
+                    }
+                    const int i = s.cvb[lo] + (g - s.coff[lo]);
+                    s.sid[t] = s.cid[lo];
                     if constexpr (FP32) {
                         const float4 v = a.vsplit[i];
                         const float2 e = a.seg_e32[i];
@@ -137,8 +218,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                         const float ay = __fadd_rn(__fsub_rn(v.y, foy), v.w);
                         s.ax[t] = ax; s.ay[t] = ay; s.ex[t] = e.x; s.ey[t] = e.y;
                         s.inv[t] = a.seg_inv32[i];
-                        mag = fmaxf(mag, fmaxf(fmaxf(fabsf(ax), fabsf(ay)),
-                                               fmaxf(fabsf(ax + e.x), fabsf(ay + e.y))));
+                        mag = fmaxf(mag, fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(ax + e.x), fabsf(ay + e.y))));
                     } else {
                         const double2 v = a.verts[i];
                         const double2 e = a.seg_e64[i];
@@ -147,54 +227,43 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                     }
                 }
                 __syncwarp();
-                const int sg = choose_group(np, ns, 1);
+                const int sg = choose_group(np, ns, 2);
                 const int lg = __ffs(sg) - 1, pg = 32 >> lg;
                 const int sub = lane & (sg - 1), grp = lane >> lg;
                 for (int q0 = 0; q0 < np; q0 += pg) {
                     const int q = q0 + grp;
-                    T m = INF;
+                    Best<T> st{INF, INF, -1};
                     if (q < np) {
                         const T px = s.px[q], py = s.py[q];
                         for (int t = sub; t < ns; t += sg)
-                            m = tmin(m, seg_d2(px, py, s.ax[t], s.ay[t], s.ex[t], s.ey[t], s.inv[t]));
+                            consider<FP32>(st, seg_d2(px, py, s.ax[t], s.ay[t], s.ex[t], s.ey[t], s.inv[t]), s.sid[t]);
                     }
-                    for (int o = sg >> 1; o > 0; o >>= 1) m = tmin(m, __shfl_xor_sync(FULL, m, o));
-                    if (sub == 0 && q < np) s.cur[q] = tmin(s.cur[q], m);
+                    for (int o = sg >> 1; o > 0; o >>= 1) st = merge<FP32>(st, shfl_best<FP32>(st, o));
+                    if (sub == 0 && q < np) {
+                        Best<T> cur{s.b1[q], s.b2[q], s.i1[q]};
+                        cur = merge<FP32>(cur, st);
+                        s.b1[q] = cur.b1; s.b2[q] = cur.b2; s.i1[q] = cur.i1;
+                    }
                 }
                 __syncwarp();
             }
-            if constexpr (FP32) {
+        }
+        if constexpr (FP32) {
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(FULL, mag, o));
-            }
-            for (int q = lane; q < np; q += 32) {
-                const T d = sqrt(s.cur[q]);
-                s.cur[q] = INF;
-                if constexpr (FP32) {
-                    const float m = fmaxf(mag, fmaxf(fabsf(s.px[q]), fabsf(s.py[q])));
-                    const float e = fmaf(64.0f * U32, m, 4.0f * a.eps_abs);
-                    if (d < s.d1[q]) {
-                        s.d2[q] = s.d1[q]; s.e2[q] = s.e1[q];
-                        s.d1[q] = d; s.e1[q] = e; s.id1[q] = lid;
-                    } else if (d < s.d2[q]) {
-                        s.d2[q] = d; s.e2[q] = e;
-                    }
-                } else {
-                    if (d < s.d1[q]) { s.d1[q] = d; s.id1[q] = lid; }
-                }
-            }
-            __syncwarp();
+            for (int o = 16; o > 0; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(FULL, mag, o));
         }
         for (int q = lane; q < np; q += 32) {
-            const int id = s.id1[q];
+            const int id = s.i1[q];
             if (id < 0) continue;
-            const double d = (double)s.d1[q];
+            const double d = (double)sqrt(s.b1[q]);
             if constexpr (FP32) {
-                const double e1 = s.e1[q], e2 = s.e2[q];
+                const double e = (double)fmaf(64.0f * U32, fmaxf(mag, fmaxf(fabsf(s.px[q]), fabsf(s.py[q]))),
+                                              4.0f * a.eps_abs);
+                const double d2 = (double)sqrtf(s.b2[q]);
                 const double tiny = 1e-12 * (a.D + 1.0);
-                if (d - e1 > a.D + tiny) continue;                                  // certainly outside the window
-                const bool in_window = d + e1 < a.D - tiny;
-                const bool separated = (double)s.d2[q] - d > e1 + e2 + tiny;       // d2 = inf: no runner-up
+                if (d - e > a.D + tiny) continue;                      // certainly outside the window
+                const bool in_window = d + e < a.D - tiny;
+                const bool separated = d2 - d > 2.0 * e + tiny;         // d2 = inf: no runner-up
                 if (!(in_window && separated)) {
                     const int slot = atomicAdd(a.n_fb, 1);
                     a.fb[slot] = make_int2(j0 + q, c);
@@ -267,12 +336,33 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
     }
 }
 
+template <bool FP32>
+static size_t p2p_smem_bytes() {
+    return sizeof(P2PSmem<FP32>) * P2P_WARPS;
+}
+
+template <bool FP32>
+static cudaError_t p2p_prepare() {
+    static bool done = false;   // per process; the attribute is per function
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_p2p_refine<FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p2p_smem_bytes<FP32>());
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_p2p_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
     (void)warps_per_block;
-    if (form == SJ_FP32X)
-        k_p2p_refine<true><<<blocks, P2P_WARPS * 32, 0, s>>>(a);
-    else
-        k_p2p_refine<false><<<blocks, P2P_WARPS * 32, 0, s>>>(a);
+    cudaError_t e;
+    if (form == SJ_FP32X) {
+        if ((e = p2p_prepare<true>()) != cudaSuccess) return e;
+        k_p2p_refine<true><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<true>(), s>>>(a);
+    } else {
+        if ((e = p2p_prepare<false>()) != cudaSuccess) return e;
+        k_p2p_refine<false><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<false>(), s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -283,10 +373,14 @@ cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s) 
 
 int p2p_blocks_per_sm(int form) {
     int n = 0;
-    if (form == SJ_FP32X)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true>, P2P_WARPS * 32, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false>, P2P_WARPS * 32, 0);
+    if (form == SJ_FP32X) {
+        if (p2p_prepare<true>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true>, P2P_WARPS * 32, p2p_smem_bytes<true>());
+    } else {
+        if (p2p_prepare<false>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false>, P2P_WARPS * 32,
+                                                      p2p_smem_bytes<false>());
+    }
     return n > 0 ? n : 1;
 }
 

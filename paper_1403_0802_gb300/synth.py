@@ -145,6 +145,65 @@ def star_polygons(rng: np.random.Generator, n_side: int = 32, extent: float = EX
     return PolygonLayer(v, ring_off, np.arange(len(sizes) + 1, dtype=np.int64))
 
 
+def tiling(rng: np.random.Generator, nx: int, ny: int, side_median: float, side_sigma: float = 1.0,
+           side_cap: int = 1250, extent: float = EXTENT, corner_jitter: float = 0.1,
+           bulge: float = 0.1, n_giant: int = 0) -> PolygonLayer:
+    """Disjoint polygons tiling [0, extent]^2 exactly, with heavy-tailed vertex counts.
+
+    Corners of an nx x ny lattice are jittered by U(-corner_jitter, corner_jitter)
+    cells (boundary corners only along the boundary).  Every lattice side gets
+    k ~ round(lognormal(ln side_median, side_sigma)) interior points, k <= side_cap,
+    at sorted positions t along its chord, displaced perpendicular to the chord by
+    U(-1, 1) * bulge * cell * sin(pi t) (sides on the extent boundary stay straight).
+    Each side is a graph over its chord that vanishes at the corners, so tiles are
+    simple; neighbouring tiles share the identical vertex arrays of a side
+    (traversed in opposite directions), so the tiling has no gaps or overlaps.
+    The n_giant tiles drawn at random get side_cap points on all four sides, so
+    the vertex-count tail reaches about 4 * side_cap.  Polygon id = row * nx + col.
+    """
+    cw, ch = extent / nx, extent / ny
+    giant = set(map(tuple, np.stack([rng.integers(0, nx, n_giant), rng.integers(0, ny, n_giant)], 1)))
+    giant_h = {(i, j + d) for i, j in giant for d in (0, 1)}
+    giant_v = {(i + d, j) for i, j in giant for d in (0, 1)}
+    P = np.zeros((nx + 1, ny + 1, 2))
+    gx, gy = np.meshgrid(np.arange(nx + 1) * cw, np.arange(ny + 1) * ch, indexing="ij")
+    jx = rng.uniform(-corner_jitter, corner_jitter, gx.shape) * cw
+    jy = rng.uniform(-corner_jitter, corner_jitter, gy.shape) * ch
+    jx[0, :] = jx[-1, :] = 0.0
+    jy[:, 0] = jy[:, -1] = 0.0
+    P[..., 0] = gx + jx
+    P[..., 1] = gy + jy
+    scale = min(cw, ch)
+
+    def side(a, b, on_boundary, big=False):
+        k = side_cap if big else int(min(side_cap, max(0, round(rng.lognormal(math.log(side_median), side_sigma)))))
+        if k == 0:
+            return np.zeros((0, 2))
+        t = np.sort(rng.uniform(0.0, 1.0, k))
+        t = np.unique(t)
+        d = b - a
+        nrm = np.array([-d[1], d[0]]) / np.hypot(*d)
+        off = np.zeros(len(t)) if on_boundary else rng.uniform(-1.0, 1.0, len(t)) * bulge * scale * np.sin(np.pi * t)
+        return a + t[:, None] * d + off[:, None] * nrm
+
+    hside = {(i, j): side(P[i, j], P[i + 1, j], j in (0, ny), (i, j) in giant_h)
+             for i in range(nx) for j in range(ny + 1)}
+    vside = {(i, j): side(P[i, j], P[i, j + 1], i in (0, nx), (i, j) in giant_v)
+             for i in range(nx + 1) for j in range(ny)}
+    verts, sizes = [], []
+    for j in range(ny):
+        for i in range(nx):
+            ring = [P[i, j][None], hside[i, j], P[i + 1, j][None], vside[i + 1, j],
+                    P[i + 1, j + 1][None], hside[i, j + 1][::-1], P[i, j + 1][None], vside[i, j][::-1]]
+            r = np.concatenate(ring)
+            verts.append(r)
+            sizes.append(len(r))
+    v = np.ascontiguousarray(np.concatenate(verts))
+    ring_off = np.zeros(len(sizes) + 1, np.int64)
+    ring_off[1:] = np.cumsum(sizes)
+    return PolygonLayer(v, ring_off, np.arange(len(sizes) + 1, dtype=np.int64))
+
+
 # --------------------------------------------------------------------------- polylines
 
 def _segmented_cumsum(vals: np.ndarray, starts: np.ndarray) -> np.ndarray:
@@ -222,6 +281,21 @@ def p2p_walks(n_points: int = 10_000_000, n_lines: int = 100_000, seed: int = SE
     pts = points_mixture(n_points, rng)
     return Workload("p2p_10M_walks100k_D100_grid1024", "p2p", pts, grid(grid_n),
                     polylines=layer, D=float(D))
+
+
+def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE + 3,
+              grid_n: int = 1024) -> Workload:
+    """PIP at scale: clustered points against a disjoint tiling.  Layer 1: 200 x 200
+    tiles, side counts lognormal(median 2.6, sigma 1) capped at 1,250, three giant
+    tiles (polygon median ~19, max ~5,000).  Layer 2: 140 x 100 tiles, side median
+    90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000)."""
+    rng = np.random.default_rng(seed + 10 * layer)
+    if layer == 1:
+        P = tiling(rng, 200, 200, side_median=2.6, side_cap=1250, n_giant=3)
+    else:
+        P = tiling(rng, 140, 100, side_median=90.0, side_cap=25000, n_giant=3)
+    pts = points_mixture(n_points, np.random.default_rng(seed))
+    return Workload(f"pip_{n_points}_tiles{P.n_polygons}_grid{grid_n}", "pip", pts, grid(grid_n), polygons=P)
 
 
 def p2p_walks_lognormal(n_points: int = 170_000_000, n_lines: int = 150_000,

@@ -344,3 +344,47 @@ def test_fp32x_fallback_rate_is_small(api, oracle):
         api.p2p_join(layer, w.points, form="fp32x")
         st = layer.stats()
     assert st["fallbacks"] < 1e-3 * st["points"]
+
+
+@pytest.mark.parametrize("g", [
+    dict(x0=-123.456, y0=7.89, x1=99876.54, y1=100007.1, nx=1013, ny=997),
+    dict(x0=4.5e6, y0=5.3e6, x1=4.5e6 + 37123.3, y1=5.3e6 + 411.7, nx=100_003, ny=7),   # UTM-like, 0.37 m cells
+    dict(x0=0.0, y0=0.0, x1=1e5, y1=1e5, nx=1024, ny=1024),
+], ids=["odd", "utm", "bench"])
+def test_cell_ids_exact_at_cell_boundaries(api, oracle, g):
+    """The threshold-table cell id must equal the FP64 rule floor(fl(fl(x-x0)/cw))
+    exactly, including points on, and one ulp around, every cell boundary."""
+    rng = np.random.default_rng(1)
+    cw = (g["x1"] - g["x0"]) / g["nx"]
+    ch = (g["y1"] - g["y0"]) / g["ny"]
+    kx = np.unique(np.concatenate([np.arange(0, g["nx"] + 1, max(1, g["nx"] // 3000)), [0, g["nx"]]]))
+    bx = g["x0"] + kx * cw
+    xs = np.concatenate([bx, np.nextafter(bx, -np.inf), np.nextafter(bx, np.inf),
+                         rng.uniform(g["x0"] - cw, g["x1"] + cw, 2000), [g["x0"], g["x1"], -0.0, 0.0]])
+    ky = np.arange(0, g["ny"] + 1, max(1, g["ny"] // 40))
+    by = g["y0"] + ky * ch
+    ys = np.concatenate([by, np.nextafter(by, -np.inf), np.nextafter(by, np.inf), [g["y0"], g["y1"]]])
+    X, Y = np.meshgrid(xs, ys[:60])
+    pts = np.stack([X.ravel(), Y.ravel()], 1)
+    pts = np.concatenate([pts, np.stack([np.full(len(ys), xs[5]), ys], 1), [[np.nan, g["y0"]], [np.inf, g["y0"]]]])
+    cs, perm = api.bucket_points(pts, g)
+    cs, perm = to_np(cs), to_np(perm)
+    G = g["nx"] * g["ny"]
+    gpu_cell = np.full(len(pts), G, np.int64)
+    gpu_cell[perm[:cs[-1]]] = np.repeat(np.arange(G), np.diff(cs))
+    np.testing.assert_array_equal(gpu_cell, oracle.point_cells(g, pts))
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("layer", [1, 2])
+def test_pip_tiles_subset(api, oracle, form, layer):
+    """PIP at scale on a 1,000,003-point subset: the clustered mixture against
+    the 40,000-tile layer (median 19, max 5,004 vertices) and the 14,000-tile
+    layer (median ~500, max 100,004 vertices, edges staged in many chunks)."""
+    w = synth.pip_tiles(n_points=1_000_003, layer=layer)
+    P = w.polygons
+    ref, nh = oracle.pip_join(w.grid, w.points, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
+    assert nh.max() == 1 and (ref >= 0).all()          # a tiling: every point in exactly one tile
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer_:
+        got = to_np(api.pip_join(layer_, w.points, form=form))
+    np.testing.assert_array_equal(got, ref)

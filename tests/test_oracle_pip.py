@@ -217,3 +217,18 @@ def test_layer_validation(oracle):
     with pytest.raises(oracle.OracleError) as e:
         oracle.pip_mbb(g, far, ro, pro)
     assert e.value.code == oracle.GRID_COVER
+
+
+@pytest.mark.parametrize("side_median,cap", [(2.6, 50), (30.0, 400)])
+def test_synthetic_tiling_covers_every_point_once(oracle, side_median, cap):
+    """The tiling generator shares each side's vertices between neighbours, so
+    every point of the extent lies in exactly one tile -- an invariant on both
+    the generator and the crossing rule (shared edges evaluate identically)."""
+    rng = np.random.default_rng(17)
+    P = synth.tiling(rng, 12, 9, side_median=side_median, side_cap=cap, extent=1000.0, n_giant=1)
+    g = synth.grid(32, extent=1000.0)
+    pts = np.concatenate([synth.points_uniform(20000, rng, extent=1000.0), P.verts[::7]])
+    pts = pts[(pts < 1000.0).all(1)]
+    ids, nh = oracle.pip_join(g, pts, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
+    np.testing.assert_array_equal(nh, 1)
+    assert P.polygon_sizes().max() >= 4 * cap
