@@ -1,14 +1,24 @@
 """Benchmark of the grid-filtered P2P / PIP join on GB300.
 
-Default workload (N = 1): P2P, 10,000,000 clustered points against 100,000
-random-walk polylines (2-40 vertices), window D = 100 m, grid 1024 x 1024.
-One step = one join against the resident polyline layer: cell ids (a1),
-bucketing (a2), work items (a5), refinement (a7) and the scatter of results
-(a8); the layer's MBBs and candidate lists (a3, a4) are built once before the
-timed region, as in serving, and their build time is reported beside it.
+Workloads (--workload):
+  p2p    (default) P2P, 10,000,000 clustered points, 100,000 random-walk
+         polylines (2-40 vertices), window D = 100 m, grid 1024 x 1024
+  pip    PIP, 1,000,000 uniform points, 1,024 star polygons, grid 256 x 256
+  pip3   PIP at scale, 100,000,000 clustered points against the 40,000-tile
+         layer (--layer 1) or the 14,000-tile heavy-tail layer (--layer 2)
+  p2p4   P2P at scale, 170,000,000 clustered points, 150,000 lognormal walks,
+         D = --D (50, 100 or 200 m)
+  serve  continuous batching: a Poisson stream of GPS batches (1k-5M points,
+         70 % PIP against the 40,000-tile layer, 30 % P2P against the 150,000
+         walks), batched rounds vs one join call per request; p50 / p99 latency
+
+One step = one join against the resident layer: cell ids (a1), bucketing (a2),
+work items (a5), refinement (a6 / a7) with the scatter of results (a8).  The
+layer's MBBs and candidate lists (a3, a4) are built once before the timed
+region, as in serving; that build time is reported as config.layer_build_ms.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload p2p|pip] [--form fp32x|fp64]
+                    [--workload ...] [--form fp32x|fp64]
 
 Rank 0 prints one JSON line.  Under torchrun (N > 1) every rank joins its own
 points against a replica of the layer (weak scaling, no data-path collective);
@@ -18,7 +28,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -32,7 +41,7 @@ sys.path.insert(0, ROOT)
 FLOPS_PER_SEGMENT = 12      # algorithmic FP ops of one point-segment distance test
 FLOPS_PER_EDGE = 2          # algorithmic FP ops of one point-edge straddle test (2 compares)
 FP32_LANES_PER_SM = 128
-FP64_LANES_PER_SM = 2       # GB300: FP64 issue rate per SM per clock (1/64 of FP32)
+FP64_LANES_PER_SM = 2       # GB300: FP64 FMA issue per SM per clock (measured: 1.97)
 
 
 def parse():
@@ -41,24 +50,32 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["p2p", "pip"], default="p2p")
+    ap.add_argument("--workload", choices=["p2p", "pip", "pip3", "p2p4", "serve"], default="p2p")
+    ap.add_argument("--layer", type=int, default=1, help="pip3: tiling layer 1 or 2")
+    ap.add_argument("--D", type=float, default=100.0, help="p2p4: window")
+    ap.add_argument("--points", type=int, default=0, help="override the workload's point count")
     ap.add_argument("--form", choices=["fp32x", "fp64"], default="fp32x")
+    ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64, e2e and CPU comparison legs")
     return ap.parse_args()
 
 
-def workload(name: str, rank: int = 0):
+def workload(args, rank: int = 0):
     from paper_1403_0802_gb300 import synth
-    if name == "p2p":
-        return synth.p2p_walks(seed=synth.SEED_BASE + 2 + 1000 * rank)
-    return synth.pip_stars(seed=synth.SEED_BASE + 1 + 1000 * rank)
+    n = args.points or None
+    if args.workload == "p2p":
+        return synth.p2p_walks(n_points=n or 10_000_000, shard=rank)
+    if args.workload == "pip":
+        return synth.pip_stars(n_points=n or 1_000_000, shard=rank)
+    if args.workload == "pip3":
+        return synth.pip_tiles(n_points=n or 100_000_000, layer=args.layer, shard=rank)
+    if args.workload == "p2p4":
+        return synth.p2p_walks_lognormal(n_points=n or 170_000_000, D=args.D, shard=rank)
+    raise ValueError(args.workload)
 
 
 def dist_env():
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return world, rank, local
+    return int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -86,6 +103,7 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
+        self.lines = []
 
     def __enter__(self):
         try:
@@ -97,7 +115,6 @@ class ClockSampler:
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.proc:
             self.proc.terminate()
             try:
@@ -110,7 +127,7 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
+        for l in self.lines:
             f = [x.strip() for x in l.split(",")]
             if len(f) < 9:
                 continue
@@ -133,29 +150,56 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(w, sample: int, threads: int | None = None):
-    """The oracle's grid-filtered join on the host cores, on the first `sample`
-    points of the workload (candidate lists built outside the timing)."""
+def oracle_join_fn(w):
+    """The oracle's grid-filtered join for workload w (candidate lists built
+    here, outside any timing)."""
     from oracle import oracle as O
     O.build()
-    n = O.set_threads(threads)
-    pts = np.ascontiguousarray(w.points[:sample])
     if w.kind == "p2p":
         L = w.polylines
-        mbb = O.p2p_mbb(w.grid, L.verts, L.line_off)
-        cs, ci = O.cand_csr(w.grid, mbb, w.D, expand=True)
-        t0 = time.perf_counter()
-        O.p2p_grid(w.grid, pts, L.verts, L.line_off, w.D, cs, ci)
-    else:
-        P = w.polygons
-        mbb = O.pip_mbb(w.grid, P.verts, P.ring_off, P.poly_ring_off)
-        cs, ci = O.cand_csr(w.grid, mbb)
-        t0 = time.perf_counter()
-        O.pip_grid(w.grid, pts, P.verts, P.ring_off, P.poly_ring_off, cs, ci)
+        cs, ci = O.cand_csr(w.grid, O.p2p_mbb(w.grid, L.verts, L.line_off), w.D, expand=True)
+        return lambda pts: O.p2p_grid(w.grid, pts, L.verts, L.line_off, w.D, cs, ci)
+    P = w.polygons
+    cs, ci = O.cand_csr(w.grid, O.pip_mbb(w.grid, P.verts, P.ring_off, P.poly_ring_off))
+    return lambda pts: O.pip_grid(w.grid, pts, P.verts, P.ring_off, P.poly_ring_off, cs, ci)
+
+
+def cpu_baseline(w, target_wall_s: float = 1.0):
+    """The oracle on all host cores, on a bounded prefix of the workload's points
+    sized from a short probe to about target_wall_s of wall time (10-30 core-s)."""
+    from oracle import oracle as O
+    n_thr = O.set_threads(None)
+    join = oracle_join_fn(w)
+    probe = min(len(w.points), 100_000)
+    t0 = time.perf_counter()
+    join(np.ascontiguousarray(w.points[:probe]))
+    rate = probe / max(time.perf_counter() - t0, 1e-6)
+    sample = int(min(len(w.points), max(probe, rate * target_wall_s)))
+    pts = np.ascontiguousarray(w.points[:sample])
+    t0 = time.perf_counter()
+    join(pts)
     dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": "points/s", "cores": n, "kind": "oracle",
-            "sample": f"first {sample} points of the workload, grid-filtered oracle join, {n} threads, "
-                      f"{dt:.2f} s wall"}
+    return {"value": sample / dt, "unit": "points/s", "cores": n_thr, "kind": "oracle",
+            "sample": f"first {sample} points of the workload, grid-filtered oracle join on {n_thr} threads, "
+                      f"{dt:.2f} s wall ({dt * n_thr:.0f} core-s)"}
+
+
+def metric_name(kind):
+    return ("P2P points/s (grid-filtered nearest polyline within D)" if kind == "p2p"
+            else "PIP points/s (grid-filtered point-in-polygon)")
+
+
+def config_of(w, args):
+    c = {"workload": w.name, "points": int(len(w.points)), "grid": f"{w.grid['nx']}x{w.grid['ny']}",
+         "form": args.form, "launch": "per_request", "pts_per_item": 64}
+    big = len(w.points) * 16 > 129e6
+    c["l2"] = ("inputs larger than L2 (points %d MB > 129 MB); no flush" % (len(w.points) * 16 // 10 ** 6) if big
+               else "points %d MB fit in L2; steps re-read them (no flush)" % (len(w.points) * 16 // 10 ** 6))
+    if w.kind == "p2p":
+        c.update(polylines=w.polylines.n_lines, vertices=int(len(w.polylines.verts)), D=w.D)
+    else:
+        c.update(polygons=w.polygons.n_polygons, vertices=int(len(w.polygons.verts)))
+    return c
 
 
 def run_reference(args):
@@ -164,31 +208,25 @@ def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    w = workload(args.workload)
     from oracle import oracle as O
-    O.build()
+    if args.workload == "serve":
+        args.workload = "p2p"
+    w = workload(args)
     n = O.set_threads(None)
+    join = oracle_join_fn(w)
     per_step = 50_000
-    if w.kind == "p2p":
-        L = w.polylines
-        cs, ci = O.cand_csr(w.grid, O.p2p_mbb(w.grid, L.verts, L.line_off), w.D, expand=True)
-        step = lambda pts: O.p2p_grid(w.grid, pts, L.verts, L.line_off, w.D, cs, ci)
-    else:
-        P = w.polygons
-        cs, ci = O.cand_csr(w.grid, O.pip_mbb(w.grid, P.verts, P.ring_off, P.poly_ring_off))
-        step = lambda pts: O.pip_grid(w.grid, pts, P.verts, P.ring_off, P.poly_ring_off, cs, ci)
     N = len(w.points)
     slices = [np.ascontiguousarray(w.points[(k * per_step) % N:(k * per_step) % N + per_step])
               for k in range(args.warmup + args.steps)]
     for k in range(args.warmup):
-        step(slices[k])
+        join(slices[k])
     t0 = time.perf_counter()
     for k in range(args.steps):
-        step(slices[args.warmup + k])
+        join(slices[args.warmup + k])
     dt = time.perf_counter() - t0
     v = per_step * args.steps / dt
     print(json.dumps({
-        "impl": "reference", "metric": metric_name(w), "value": v, "unit": "points/s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_name(w.kind), "value": v, "unit": "points/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_of(w, args),
@@ -197,28 +235,11 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def metric_name(w):
-    return ("P2P points/s (grid-filtered nearest polyline within D)" if w.kind == "p2p"
-            else "PIP points/s (grid-filtered point-in-polygon)")
-
-
-def config_of(w, args):
-    c = {"workload": w.name, "points": int(len(w.points)), "grid": f"{w.grid['nx']}x{w.grid['ny']}",
-         "form": args.form, "launch": "per_request", "pts_per_item": 64,
-         "l2": "inputs larger than L2 (points alone 160 MB for the P2P workload); no flush"}
-    if w.kind == "p2p":
-        c.update(polylines=w.polylines.n_lines, vertices=int(len(w.polylines.verts)), D=w.D)
-    else:
-        c.update(polygons=w.polygons.n_polygons, vertices=int(len(w.polygons.verts)))
-        c["l2"] = "points 16 MB fit in L2; no flush between steps"
-    return c
-
-
-def time_joins(api, layer, w, pts, form, steps, warmup, world, dev, stream, timed=True):
+def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=True):
     import torch
     n = pts.shape[0]
-    out_id = torch.empty(n, dtype=torch.int32, device=dev)
-    out_d = torch.empty(n, dtype=torch.float64, device=dev)
+    out_id = torch.empty(n, dtype=torch.int32, device=pts.device)
+    out_d = torch.empty(n, dtype=torch.float64, device=pts.device)
 
     def one(time_refine):
         if w.kind == "p2p":
@@ -239,8 +260,56 @@ def time_joins(api, layer, w, pts, form, steps, warmup, world, dev, stream, time
     e1.record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    ms = e0.elapsed_time(e1)
-    return ms, layer.stats(), (out_id, out_d)
+    return e0.elapsed_time(e1), layer.stats()
+
+
+def build_layer(api, w, dev, stream):
+    import torch
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    if w.kind == "p2p":
+        L = w.polylines
+        v = torch.as_tensor(L.verts, device=dev)
+        off = torch.as_tensor(L.line_off, device=dev)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        layer = api.p2p_layer(v, off, w.D, w.grid, stream=stream)
+    else:
+        P = w.polygons
+        v = torch.as_tensor(P.verts, device=dev)
+        ro = torch.as_tensor(P.ring_off, device=dev)
+        pro = torch.as_tensor(P.poly_ring_off, device=dev)
+        torch.cuda.synchronize()
+        t0.record(stream)
+        layer = api.pip_layer(v, ro, pro, w.grid, stream=stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    return layer, t0.elapsed_time(t1)
+
+
+def roofline_of(w, form, st, props, peaks):
+    """Dominant kernel = the refinement launch, timed with CUDA events on the
+    join's stream.  Work per launch = the (point, edge or segment) tests the
+    kernel executes (the candidate lists' tests minus the exact staging prune)
+    x the algorithmic FP ops of one test; achieved = that / launch time.  The
+    unpruned count (SURVEY 8(d) units) is reported as effective_tflops."""
+    refine_ms = st["refine_ms"] / max(st["refine_launches"], 1)
+    joins = max(st["joins"], 1)
+    algo = st["algo_tests"] / joins
+    executed = st["edge_tests"] / joins
+    fpt = FLOPS_PER_SEGMENT if w.kind == "p2p" else FLOPS_PER_EDGE
+    lanes = FP32_LANES_PER_SM if form == "fp32x" else FP64_LANES_PER_SM
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * lanes * 2 * sm_mhz * 1e6 / 1e12
+    achieved = executed * fpt / (refine_ms / 1e3) / 1e12 if refine_ms > 0 else None
+    return {"bound": "alu", "kernel": f"k_{w.kind}_refine<{form}>", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_source": f"derived: {props.multi_processor_count} SMs x {lanes} "
+                           f"{'FP32' if form == 'fp32x' else 'FP64'} lanes x 2 flops x {sm_mhz:.0f} MHz "
+                           f"(MEASURED_PEAKS sm_max_mhz)",
+            "refine_ms_per_launch": refine_ms, "executed_tests_per_launch": executed,
+            "algorithmic_tests_per_launch": algo, "flops_per_test": fpt,
+            "effective_tflops": algo * fpt / (refine_ms / 1e3) / 1e12 if refine_ms > 0 else None}
 
 
 def run_ours(args):
@@ -254,70 +323,30 @@ def run_ours(args):
     torch.cuda.set_device(dev)
     from paper_1403_0802_gb300 import api, build
     build.build()
-    w = workload(args.workload, rank)
+    w = workload(args, rank)
     stream = torch.cuda.current_stream(dev)
-
-    t0 = torch.cuda.Event(enable_timing=True); t1 = torch.cuda.Event(enable_timing=True)
-    if w.kind == "p2p":
-        L = w.polylines
-        v = torch.as_tensor(L.verts, device=dev); off = torch.as_tensor(L.line_off, device=dev)
-        torch.cuda.synchronize(); t0.record(stream)
-        layer = api.p2p_layer(v, off, w.D, w.grid, stream=stream)
-    else:
-        P = w.polygons
-        v = torch.as_tensor(P.verts, device=dev)
-        ro = torch.as_tensor(P.ring_off, device=dev); pro = torch.as_tensor(P.poly_ring_off, device=dev)
-        torch.cuda.synchronize(); t0.record(stream)
-        layer = api.pip_layer(v, ro, pro, w.grid, stream=stream)
-    t1.record(stream); torch.cuda.synchronize()
-    layer_ms = t0.elapsed_time(t1)
-
+    layer, layer_ms = build_layer(api, w, dev, stream)
     pts = torch.as_tensor(w.points, device=dev)
     n = pts.shape[0]
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if os.environ.get(
-        "CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    gpu_index = int(vis) if vis.isdigit() else local
     with ClockSampler(gpu_index) as clk:
-        ms, st, _ = time_joins(api, layer, w, pts, args.form, args.steps, args.warmup, world, dev, stream)
+        ms, st = time_joins(api, layer, w, pts, args.form, args.steps, args.warmup, world, stream)
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world, dev)
     value = n * world * args.steps / (ms_max / 1000.0)
-
-    # dominant kernel: the refinement launch, timed with events on the join's stream
-    refine_ms = st["refine_ms"] / max(st["refine_launches"], 1)
-    tests_per_launch = st["edge_tests"] / max(st["joins"], 1)
     props = torch.cuda.get_device_properties(dev)
-    peaks = measured_peaks()
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    if w.kind == "p2p":
-        flops = tests_per_launch * FLOPS_PER_SEGMENT
-        lanes = FP32_LANES_PER_SM if args.form == "fp32x" else FP64_LANES_PER_SM
-    else:
-        flops = tests_per_launch * FLOPS_PER_EDGE
-        lanes = FP32_LANES_PER_SM if args.form == "fp32x" else FP64_LANES_PER_SM
-    peak_tflops = props.multi_processor_count * lanes * 2 * sm_mhz * 1e6 / 1e12
-    achieved = flops / (refine_ms / 1000.0) / 1e12 if refine_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": f"k_{w.kind}_refine<{args.form}>", "achieved": achieved,
-                "peak": peak_tflops, "unit": "TFLOP/s",
-                "frac": (achieved / peak_tflops) if achieved else None, "traffic": None,
-                "peak_source": f"derived: {props.multi_processor_count} SMs x {lanes} "
-                               f"{'FP32' if args.form == 'fp32x' else 'FP64'} lanes x 2 x {sm_mhz:.0f} MHz",
-                "refine_ms_per_launch": refine_ms, "tests_per_launch": tests_per_launch,
-                "flops_per_test": FLOPS_PER_SEGMENT if w.kind == "p2p" else FLOPS_PER_EDGE}
+    roofline = roofline_of(w, args.form, st, props, measured_peaks())
 
-    extra = {}
-    if not args.no_baselines and rank == 0:
-        # the plain FP64 form, same workload, fewer steps
-        if args.form != "fp64":
-            k64 = max(3, min(args.steps, 20))
-            ms64, st64, _ = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, dev, stream)
-            extra["fp64_plain"] = {"value": n * k64 / (ms64 / 1000.0), "unit": "points/s",
-                                   "ms_per_step": ms64 / k64,
-                                   "refine_ms_per_launch": st64["refine_ms"] / max(st64["refine_launches"], 1)}
-            extra["speedup_vs_fp64_plain"] = value / extra["fp64_plain"]["value"]
-        extra["fallbacks_per_join"] = st["fallbacks"] / max(st["joins"], 1)
-        extra["edge_tests_per_s"] = tests_per_launch * args.steps / (ms / 1000.0)
+    extra = {"fallbacks_per_join": st["fallbacks"] / max(st["joins"], 1),
+             "edge_tests_per_s_algorithmic": st["algo_tests"] / (ms / 1000.0)}
+    if not args.no_baselines and rank == 0 and args.form != "fp64":
+        k64 = max(3, min(args.steps, 20))
+        ms64, st64 = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, stream)
+        extra["fp64_plain"] = {"value": n * k64 / (ms64 / 1000.0), "unit": "points/s", "ms_per_step": ms64 / k64,
+                               "roofline": roofline_of(w, "fp64", st64, props, measured_peaks())}
+        extra["speedup_vs_fp64_plain"] = value / extra["fp64_plain"]["value"]
 
-    # end to end through the C ABI with pinned host buffers
     e2e = None
     if rank == 0 and not args.no_baselines:
         hp = torch.empty((n, 2), dtype=torch.float64, pin_memory=True)
@@ -325,34 +354,32 @@ def run_ours(args):
         hid = torch.empty(n, dtype=torch.int32, pin_memory=True)
         hd = torch.empty(n, dtype=torch.float64, pin_memory=True)
         ke = max(3, min(args.steps, 20))
-        join_host = (lambda: api.p2p_join_host(layer, hp, hid, hd, form=args.form, stream=stream)) if w.kind == "p2p" \
-            else (lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream))
+        if w.kind == "p2p":
+            join_host = lambda: api.p2p_join_host(layer, hp, hid, hd, form=args.form, stream=stream)
+        else:
+            join_host = lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream)
         for _ in range(2):
             join_host()
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        t0 = time.perf_counter()
         for _ in range(ke):
-            join_host()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ems = e0.elapsed_time(e1)
+            join_host()      # synchronous: copies in, join, copies out
+        ems = (time.perf_counter() - t0) * 1e3
         e2e = {"value": n * ke / (ems / 1000.0), "unit": "points/s", "h2d_bytes_per_step": n * 16,
                "d2h_bytes_per_step": n * (4 + (8 if w.kind == "p2p" else 0)), "steps": ke,
-               "api": "sj_p2p_join_host" if w.kind == "p2p" else "sj_pip_join_host"}
+               "api": "sj_p2p_join_host" if w.kind == "p2p" else "sj_pip_join_host",
+               "timing": "host wall clock around synchronous calls (pinned buffers)"}
 
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_baselines:
-        cpu = cpu_baseline(w, 1_000_000 if w.kind == "p2p" else 1_000_000)
-
+    cpu = cpu_baseline(w) if (rank == 0 and world == 1 and not args.no_baselines) else None
     kernels_per_join = 5 + 1 + (1 if (w.kind == "p2p" and args.form == "fp32x") else 0)
     if rank == 0:
         line = {
-            "metric": metric_name(w), "value": value, "unit": "points/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.form == "fp32x" else "f64",
-            "data": "synthetic", "config": dict(config_of(w, args), layer_build_ms=layer_ms,
-                                                 parallelism=f"points sharded, layer replicated x{world}"),
+            "metric": metric_name(w.kind), "value": value, "unit": "points/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.form == "fp32x" else "f64", "data": "synthetic",
+            "config": dict(config_of(w, args), layer_build_ms=layer_ms,
+                           parallelism=f"points sharded, layer replicated x{world}"),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": kernels_per_join * args.steps, **extra,
         }
@@ -363,10 +390,58 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_serve(args):
+    """Continuous batching vs one join call per request on the same stream."""
+    import torch
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_1403_0802_gb300 import api, build, serve, synth
+    build.build()
+    torch.cuda.set_device(local)
+    wp = synth.pip_tiles(n_points=20_000_000, layer=1)
+    wl = synth.p2p_walks_lognormal(n_points=20_000_000, n_lines=150_000, D=100.0)
+    pip = api.pip_layer(wp.polygons.verts, wp.polygons.ring_off, wp.polygons.poly_ring_off, wp.grid)
+    p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
+    pool_p = torch.from_numpy(wp.points).pin_memory()
+    pool_l = torch.from_numpy(wl.points).pin_memory()
+    srv = serve.Server(pip, p2p, form=args.form, round_points=24_000_000, max_requests=4096)
+    # warm-up: workspaces, graphs, pools
+    warm = serve.make_stream(32, 0.0, pool_p, pool_l, seed=1)
+    srv.run(warm, mode="batched")
+    srv.run(serve.make_stream(8, 0.0, pool_p, pool_l, seed=2), mode="per_request")
+    # capacity of the per-request form at saturation sets the arrival rate
+    sat = srv.run(serve.make_stream(min(args.requests, 300), 0.0, pool_p, pool_l, seed=3), mode="per_request")
+    mean_pts = sat["points"] / sat["requests"]
+    res = {}
+    for rho in (0.5, 0.8):
+        rate = rho * sat["points_per_s"] / mean_pts
+        for mode in ("per_request", "batched"):
+            reqs = serve.make_stream(args.requests, rate, pool_p, pool_l, seed=7)
+            res[f"{mode}_rho{rho}"] = srv.run(reqs, mode=mode)
+    b, p = res["batched_rho0.8"], res["per_request_rho0.8"]
+    line = {"metric": "serving p50/p99 latency (ms) and points/s, continuous batching", "value": b["p99_ms"],
+            "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests, "warmup": 40, "ms_per_step": b["mean_ms"],
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.form == "fp32x" else "f64", "data": "synthetic",
+            "config": {"workload": f"serve_{args.requests}req_pip40k_p2p150k", "requests": args.requests,
+                       "sizes": "log-uniform 1e3..5e6 points", "mix": "70% PIP / 30% P2P (D=100 m)",
+                       "arrivals": "Poisson, rate = rho x per-request capacity", "form": args.form},
+            "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "points_per_s": b["points_per_s"],
+            "per_request_p50_ms": p["p50_ms"], "per_request_p99_ms": p["p99_ms"],
+            "per_request_points_per_s": p["points_per_s"], "saturation_per_request": sat, "runs": res}
+    print(json.dumps(line))
+    srv.close()
+    pip.close()
+    p2p.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -114,6 +114,10 @@ typedef struct {
     int64_t hits;          /* points given an id                                 */
     int64_t refine_launches; /* refinement launches timed (SJ_FLAG_TIME_REFINE)  */
     double refine_ms;        /* their summed device time, milliseconds           */
+    int64_t algo_tests;      /* edge / segment tests the candidate lists imply;
+                                edge_tests is what remains after the exact
+                                per-item prune (edges that cannot straddle /
+                                segments farther than D from every point)        */
 } sj_run_stats;
 
 /* Build a resident polygon layer and its candidate lists (Sec. III.A: MBB of
@@ -191,6 +195,51 @@ sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32
 /* Counters of the joins run on `layer` (synchronises the device). */
 sj_status sj_layer_get_stats(const sj_layer *layer, sj_run_stats *out);
 sj_status sj_layer_reset_stats(sj_layer *layer);
+
+/* ------------------------------------------------------------------ batched rounds
+ *
+ * Continuous batching: an engine joins many requests per call ("round").
+ * Requests against the same layer are joined as one point set -- one cell-id
+ * pass, one scan, one scatter, ONE refinement launch over their merged work
+ * items and one pass that writes each request's outputs -- so a round costs
+ * a fixed number of launches per layer whatever the number of requests.  The
+ * per-layer kernel sequence has a fixed shape (sizes live in device memory),
+ * is captured into a CUDA graph on its first round and replayed afterwards.
+ * Results are exactly those of joining each request alone (Sec. III.B-C:
+ * a point's result depends only on the point and the layer). */
+
+typedef struct sj_engine sj_engine;
+
+typedef struct {
+    const sj_layer *layer;   /* polygon layer (PIP) or polyline layer (P2P)      */
+    const double *pts;       /* dev [N, 2] f64, 16-byte aligned                   */
+    int64_t N;
+    int32_t *out_id;         /* dev [N] int32                                     */
+    double *out_d;           /* dev [N] f64 for polyline layers (may be NULL)     */
+} sj_request;
+
+/* opts.flags for sj_engine_create: launch the round's kernels directly instead
+ * of replaying a captured graph. */
+#define SJ_FLAG_NO_GRAPH 2
+
+/* Create an engine for rounds of at most max_points points and max_requests
+ * requests per layer.  opts selects form and points per work item (as for the
+ * joins; NULL = defaults).  The engine allocates one workspace per layer on
+ * the first round that uses the layer (about 52 bytes per point plus 8 bytes
+ * per grid cell) and captures that layer's graph then; later rounds allocate
+ * nothing.  Layers must outlive the engine.  Errors: SJ_ERR_INVALID. */
+sj_status sj_engine_create(int64_t max_points, int32_t max_requests, const sj_opts *opts, sj_engine **out);
+
+/* One round over reqs[0..n): asynchronous on stream (a non-NULL stream is
+ * needed for graph replay; the legacy stream runs the kernels directly).  The
+ * host blocks only if the request table of the round-before-last for the same
+ * layer has not been copied to the device yet.  Rounds on one engine must be
+ * issued on one stream (or ordered by the caller).  Errors: SJ_ERR_INVALID
+ * (sizes beyond the engine's limits, bad buffers), SJ_ERR_CUDA, SJ_ERR_OOM. */
+sj_status sj_engine_round(sj_engine *engine, const sj_request *reqs, int32_t n, void *stream);
+
+/* Free the engine (synchronises the device first).  NULL is a no-op. */
+sj_status sj_engine_destroy(sj_engine *engine);
 
 /* P2P join that allocates nothing.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory when they join

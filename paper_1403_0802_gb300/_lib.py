@@ -33,7 +33,7 @@ class sj_layer_info(C.Structure):
 class sj_run_stats(C.Structure):
     _fields_ = [("joins", C.c_int64), ("points", C.c_int64), ("items", C.c_int64), ("pairs", C.c_int64),
                 ("edge_tests", C.c_int64), ("fallbacks", C.c_int64), ("hits", C.c_int64),
-                ("refine_launches", C.c_int64), ("refine_ms", C.c_double)]
+                ("refine_launches", C.c_int64), ("refine_ms", C.c_double), ("algo_tests", C.c_int64)]
 
 
 class sj_peak_rates(C.Structure):
@@ -42,10 +42,16 @@ class sj_peak_rates(C.Structure):
                 ("dfma_per_clk_sm", C.c_double), ("dadd_per_s", C.c_double), ("dadd_per_clk_sm", C.c_double)]
 
 
+class sj_request(C.Structure):
+    _fields_ = [("layer", C.c_void_p), ("pts", C.c_void_p), ("N", C.c_int64), ("out_id", C.c_void_p),
+                ("out_d", C.c_void_p)]
+
+
 SJ_OK, SJ_ERR_INVALID, SJ_ERR_OOM, SJ_ERR_GRID_COVER, SJ_ERR_CUDA, SJ_ERR_TIMEOUT, SJ_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
 SJ_FP64, SJ_FP32X = 0, 1
 SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
 SJ_FLAG_TIME_REFINE = 1
+SJ_FLAG_NO_GRAPH = 2
 
 # name -> (restype, argtypes); every name here is declared in include/sj.h
 _P, _I32, _I64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
@@ -67,6 +73,9 @@ SIGNATURES = {
     "sj_last_error": (C.c_char_p, []),
     "sj_version": (C.c_char_p, []),
     "sj_peaks_measure": (C.c_int, [C.POINTER(sj_peak_rates)]),
+    "sj_engine_create": (C.c_int, [_I64, _I32, C.POINTER(sj_opts), _LP]),
+    "sj_engine_round": (C.c_int, [_P, C.POINTER(sj_request), _I32, _P]),
+    "sj_engine_destroy": (C.c_int, [_P]),
 }
 
 

@@ -226,5 +226,51 @@ def p2p_join_once(points, verts, line_off, D: float, grid: dict, form: str = "fp
         return res
 
 
+class Engine:
+    """Batched rounds (continuous batching) over resident layers.
+
+        eng = Engine(max_points=8_000_000, max_requests=256, form="fp32x")
+        eng.round([(pip_layer, pts_a, ids_a, None), (p2p_layer, pts_b, ids_b, d_b)], stream)
+
+    Each request is (layer, points [N, 2] f64 CUDA tensor, out_id int32 [N],
+    out_d f64 [N] or None); outputs are written asynchronously on `stream`.
+    """
+
+    def __init__(self, max_points: int, max_requests: int = 1024, form: str = "fp64", pts_per_item: int = 0,
+                 graph: bool = True):
+        o = L.sj_opts(FORMS[form], L.SJ_PERSISTENT, 0, int(pts_per_item), 0, 0 if graph else L.SJ_FLAG_NO_GRAPH)
+        h = C.c_void_p()
+        L.check(L.lib().sj_engine_create(int(max_points), int(max_requests), C.byref(o), C.byref(h)),
+                "sj_engine_create")
+        self._h = h
+        self.max_points = int(max_points)
+        self.max_requests = int(max_requests)
+        self.form = form
+
+    def round(self, requests, stream=None):
+        arr = (L.sj_request * max(len(requests), 1))()
+        for k, (layer, pts, out_id, out_d) in enumerate(requests):
+            arr[k] = L.sj_request(layer.handle.value, _ptr(pts), pts.shape[0], _ptr(out_id),
+                                  _ptr(out_d) if out_d is not None else None)
+        L.check(L.lib().sj_engine_round(self._h, arr, len(requests), _stream(stream)), "sj_engine_round")
+
+    def close(self):
+        if self._h:
+            L.lib().sj_engine_destroy(self._h)
+            self._h = C.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
 def version() -> str:
     return L.lib().sj_version().decode()

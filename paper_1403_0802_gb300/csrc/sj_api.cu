@@ -12,8 +12,7 @@
 #include <utility>
 #include <vector>
 
-#include "sj.h"
-#include "sj_internal.cuh"
+#include "sj_host.hpp"
 
 namespace sj {
 cudaError_t launch_check_offsets(const int64_t *off, int64_t n, int64_t min_size, int64_t first, int64_t last, int *out,
@@ -22,86 +21,40 @@ cudaError_t launch_check_finite(const double2 *v, int n, int *bad, cudaStream_t 
 cudaError_t launch_pip_topology(const int *ring_off, int R, const int *poly_ring_off, int P, int *poly_voff, int *nxt,
                                 cudaStream_t s);
 cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s);
-cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
-                             float *inv32, cudaStream_t s);
+cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float4 *seg32,
+                             cudaStream_t s);
 cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s);
 cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
+cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
 int p2p_blocks_per_sm(int form);
 }  // namespace sj
 
 using namespace sj;
 
-struct sj_layer {
-    int kind = 0;
-    int device = 0;
-    sj_grid grid{};
-    GridDev g{};
-    int nobj = 0;
-    int V = 0;
-    int64_t R = 0;
-    double D = 0.0;
-    int64_t M = 0;
-    float eps_abs = 0.0f;
-    double2 *verts = nullptr;
-    float4 *vsplit = nullptr;
-    int *obj_voff = nullptr;
-    int *nxt = nullptr;
-    int *ring_off = nullptr;
-    int *poly_ring_off = nullptr;
-    double2 *seg_e64 = nullptr;
-    double *seg_inv64 = nullptr;
-    float2 *seg_e32 = nullptr;
-    float *seg_inv32 = nullptr;
-    Box *mbb = nullptr;
-    int *cand_start = nullptr;
-    int *cand_ids = nullptr;
-    unsigned long long *stats = nullptr;
-    unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
-    mutable std::atomic<long long> joins{0};
-    mutable std::atomic<long long> points{0};
-    // SJ_FLAG_TIME_REFINE: event pairs recorded around refinement launches,
-    // resolved (and destroyed) by sj_layer_get_stats.
-    mutable std::mutex ev_mu;
-    mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
-    mutable double refine_ms = 0.0;
-    mutable long long refine_launches = 0;
-};
 
 // ------------------------------------------------------------------ errors
 
 static thread_local std::string g_err;
 
-static sj_status fail(sj_status st, const std::string &msg) {
+sj_status sj::fail(sj_status st, const std::string &msg) {
     g_err = msg;
     return st;
 }
 
-static sj_status cuda_fail(cudaError_t e, const char *what) {
+sj_status sj::cuda_fail(cudaError_t e, const char *what) {
     return fail(e == cudaErrorMemoryAllocation ? SJ_ERR_OOM : SJ_ERR_CUDA,
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-#define CUDA_TRY(x)                                    \
-    do {                                               \
-        cudaError_t e_ = (x);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_, #x); \
-    } while (0)
-
 // ------------------------------------------------------------------ device info
 
-struct DevInfo {
-    int sms = 0;
-    int pip_bps[2] = {0, 0};
-    int p2p_bps[2] = {0, 0};
-    bool init = false;
-};
 static DevInfo g_dev[64];
 static std::mutex g_dev_mu;
 
-static sj_status device_info(int dev, DevInfo **out) {
+sj_status sj::device_info(int dev, DevInfo **out) {
     if (dev < 0 || dev >= 64) return fail(SJ_ERR_INVALID, "device index out of range");
     std::lock_guard<std::mutex> lk(g_dev_mu);
     DevInfo &d = g_dev[dev];
@@ -153,29 +106,43 @@ static sj_status layer_tables(sj_layer *L, cudaStream_t s) {
     CUDA_TRY(launch_thresholds(L->g, L->cell_keys, L->cell_keys + L->g.nx + 1, s));
     L->g.kx = L->cell_keys;
     L->g.ky = L->cell_keys + L->g.nx + 1;
+    CUDA_TRY(cudaMalloc((void **)&L->frames, sizeof(float) * ((size_t)L->g.nx + L->g.ny)));
+    CUDA_TRY(launch_frames(L->g, L->frames, L->frames + L->g.nx, s));
+    L->xmax = std::max(std::max(std::fabs(L->grid.x0), std::fabs(L->grid.x1)),
+                       std::max(std::fabs(L->grid.y0), std::fabs(L->grid.y1)));
     return SJ_OK;
 }
 
-static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+// FP32 float at or below (down) / at or above (up) the double x.
+static float float_down(double x) {
+    float f = (float)x;
+    return ((double)f > x) ? std::nextafter(f, -INFINITY) : f;
+}
+static float float_up(double x) {
+    float f = (float)x;
+    return ((double)f < x) ? std::nextafter(f, INFINITY) : f;
+}
 
-// Stream-ordered scratch carved from one allocation.
-struct Scratch {
-    char *base = nullptr;
-    size_t off = 0;
-    template <class T>
-    T *take(size_t n) {
-        off = (off + 255) & ~(size_t)255;
-        T *p = (T *)(base + off);
-        off += n * sizeof(T);
-        return p;
-    }
-};
-
-template <class F>
-static size_t measure(F f) {
-    Scratch s;
-    f(s);
-    return s.off + 256;
+// Layer-dependent fields of the refinement arguments.
+void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
+    ra.g = L->g;
+    ra.cand_start = L->cand_start;
+    ra.cand_ids = L->cand_ids;
+    ra.obj_voff = L->obj_voff;
+    ra.nxt = L->nxt;
+    ra.verts = L->verts;
+    ra.vsplit = L->vsplit;
+    ra.seg_e64 = L->seg_e64;
+    ra.seg_inv64 = L->seg_inv64;
+    ra.seg32 = L->seg32;
+    ra.D = L->D;
+    ra.Df = L->Df;
+    ra.Ddn = L->Ddn;
+    ra.Dup = L->Dup;
+    ra.eps_abs = L->eps_abs;
+    ra.frame_x = L->frames;
+    ra.frame_y = L->frames + L->g.nx;
+    ra.stats = L->stats;
 }
 
 // ------------------------------------------------------------------ layers
@@ -198,7 +165,8 @@ static void resolve_events(const sj_layer *L) {
 static void layer_free(sj_layer *L) {
     resolve_events(L);
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
-                    L->seg_inv64, L->seg_e32, L->seg_inv32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys};
+                    L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
+                    L->frames};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -285,12 +253,15 @@ static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
         CUDA_TRY(cudaMemsetAsync(L->cand_start, 0, sizeof(int) * ((size_t)L->g.G + 1), s));
     }
     CUDA_TRY(cudaStreamSynchronize(s));
-    // eps_abs bounds 2 |lo part| + rounding of the hi/lo split for any vertex
-    // inside the grid box: 2.0003 u^2 max|coordinate|.
-    double xm = std::max(std::max(std::fabs(L->grid.x0), std::fabs(L->grid.x1)),
-                         std::max(std::fabs(L->grid.y0), std::fabs(L->grid.y1)));
+    // The cell-relative coordinate rel = fl32(fl32(hi - o) + lo) of any value v
+    // in the grid box satisfies |rel - (v - o)| <= 2.0001 u |rel| + eps_abs with
+    // eps_abs = 6.0001 u^2 max|coordinate| (the truncation remainder |lo| is
+    // below 2u |v|, rounded once more by the conversion); 8 u^2 is used.
     double u = 5.9604644775390625e-08;
-    L->eps_abs = (float)(2.0003 * u * u * xm * (1.0 + 1e-6)) + 1e-30f;
+    L->eps_abs = (float)(8.0 * u * u * L->xmax * (1.0 + 1e-6)) + 1e-30f;
+    L->Df = (float)L->D;
+    L->Ddn = float_down(L->D * (1.0 - 1e-12));
+    L->Dup = float_up(L->D * (1.0 + 1e-12) + 1e-300);
     return SJ_OK;
 }
 
@@ -401,11 +372,10 @@ extern "C" sj_status sj_p2p_layer_create(const double *verts, int64_t V, const i
     CUDA_TRY(dalloc(&L->vsplit, (size_t)V));
     CUDA_TRY(dalloc(&L->seg_e64, (size_t)V));
     CUDA_TRY(dalloc(&L->seg_inv64, (size_t)V));
-    CUDA_TRY(dalloc(&L->seg_e32, (size_t)V));
-    CUDA_TRY(dalloc(&L->seg_inv32, (size_t)V));
+    CUDA_TRY(dalloc(&L->seg32, (size_t)V));
     if (V > 0) {
         CUDA_TRY(launch_split(L->verts, (int)V, L->vsplit, s));
-        CUDA_TRY(launch_seg_table(L->verts, L->obj_voff, Lc, L->seg_e64, L->seg_inv64, L->seg_e32, L->seg_inv32, s));
+        CUDA_TRY(launch_seg_table(L->verts, L->obj_voff, Lc, L->seg_e64, L->seg_inv64, L->seg32, s));
     }
     CUDA_TRY(dalloc(&L->stats, ST_N));
     CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));
@@ -457,6 +427,7 @@ extern "C" sj_status sj_layer_get_stats(const sj_layer *L, sj_run_stats *out) {
     out->edge_tests = (int64_t)h[ST_TESTS];
     out->fallbacks = (int64_t)h[ST_FALLBACK];
     out->hits = (int64_t)h[ST_HITS];
+    out->algo_tests = (int64_t)h[ST_ALGO];
     return SJ_OK;
 }
 
@@ -504,6 +475,8 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
     int launch = o ? o->launch : SJ_PER_REQUEST;
     if (launch != SJ_PER_REQUEST && launch != SJ_PERSISTENT) return fail(SJ_ERR_INVALID, "unknown launch form");
+    if (form == SJ_FP32X && L->xmax > 1e30)
+        return fail(SJ_ERR_INVALID, "SJ_FP32X needs grid coordinates below 1e30 in magnitude; use SJ_FP64");
     int ch = (o && o->pts_per_item) ? o->pts_per_item : 64;
     if (ch < 1 || ch > MAX_CH) return fail(SJ_ERR_INVALID, "pts_per_item must be in 1..128");
     int dev = 0;
@@ -546,30 +519,17 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     if (e == cudaSuccess) e = launch_bucket(ba, s);
 
     RefineArgs ra{};
-    ra.g = L->g;
+    fill_refine(L, ra);
     ra.items = b.items;
     ra.n_items = b.totals + 1;
     ra.cell_start = b.cell_start;
     ra.perm = b.perm;
     ra.spts = b.spts;
-    ra.cand_start = L->cand_start;
-    ra.cand_ids = L->cand_ids;
-    ra.obj_voff = L->obj_voff;
-    ra.nxt = L->nxt;
-    ra.verts = L->verts;
-    ra.vsplit = L->vsplit;
-    ra.seg_e64 = L->seg_e64;
-    ra.seg_inv64 = L->seg_inv64;
-    ra.seg_e32 = L->seg_e32;
-    ra.seg_inv32 = L->seg_inv32;
-    ra.D = L->D;
-    ra.eps_abs = L->eps_abs;
     ra.ch = ch;
     ra.out_id = out_id;
     ra.out_d = out_d;
     ra.fb = b.fb;
     ra.n_fb = b.totals + 2;
-    ra.stats = L->stats;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     const bool timed = o && (o->flags & SJ_FLAG_TIME_REFINE);
     if (e == cudaSuccess && timed) {
@@ -795,29 +755,17 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     CUDA_TRY(launch_bucket(ba, s));
 
     RefineArgs ra{};
-    ra.g = L->g;
+    fill_refine(L, ra);
     ra.items = b.items;
     ra.n_items = b.totals + 1;
     ra.cell_start = b.cell_start;
     ra.perm = b.perm;
     ra.spts = b.spts;
-    ra.cand_start = L->cand_start;
-    ra.cand_ids = L->cand_ids;
-    ra.obj_voff = L->obj_voff;
-    ra.verts = L->verts;
-    ra.vsplit = L->vsplit;
-    ra.seg_e64 = L->seg_e64;
-    ra.seg_inv64 = L->seg_inv64;
-    ra.seg_e32 = L->seg_e32;
-    ra.seg_inv32 = L->seg_inv32;
-    ra.D = L->D;
-    ra.eps_abs = L->eps_abs;
     ra.ch = NOALLOC_CH;
     ra.out_id = out_id;
     ra.out_d = out_d;
     ra.fb = b.fb;
     ra.n_fb = b.totals + 2;
-    ra.stats = L->stats;
     CUDA_TRY(launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s));
     if (need_fb) CUDA_TRY(launch_p2p_recheck(ra, di->sms * 4, s));
     L->joins++;

@@ -159,16 +159,41 @@ cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned
 // a1: cell id per point and per-cell count; the atomic's return value is the
 // point's rank inside its cell, so the scatter needs no second pass.  The
 // outputs are initialised here (-1 / +inf), refinement overwrites the hits.
+// Each thread handles UNR points per step (indices i, i + T, ..., T = total
+// threads) so that several independent load -> atomic -> store chains are in
+// flight at once.
+constexpr int UNR = 4;
+
 __global__ void k_cell_hist(BucketArgs a) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        double2 p = a.pts[i];
-        int c = point_cell(a.g, p.x, p.y);
-        int r = 0;
-        if (c < a.g.G) r = atomicAdd(&a.cnt[c], 1);
-        a.key_rank[i] = make_int2(c, r);
-        if (a.out_id) a.out_id[i] = -1;
-        if (a.out_d) a.out_d[i] = inf;
+    const int T = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+        double2 p[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            if (i < a.n) p[u] = a.pts[i];
+        }
+        int c[UNR], r[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            c[u] = a.g.G;
+            r[u] = 0;
+            if (i < a.n) {
+                c[u] = point_cell(a.g, p[u].x, p[u].y);
+                if (c[u] < a.g.G) r[u] = atomicAdd(&a.cnt[c[u]], 1);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            if (i < a.n) {
+                a.key_rank[i] = make_int2(c[u], r[u]);
+                if (a.out_id) a.out_id[i] = -1;
+                if (a.out_d) a.out_d[i] = inf;
+            }
+        }
     }
 }
 
@@ -198,12 +223,28 @@ struct BucketApply {
 };
 
 __global__ void k_scatter(BucketArgs a) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += gridDim.x * blockDim.x) {
-        int2 k = a.key_rank[i];
-        if (k.x < a.g.G) {
-            int pos = a.cell_start[k.x] + k.y;
-            a.perm[pos] = i;
-            if (a.spts) a.spts[pos] = a.pts[i];
+    const int T = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+        int2 k[UNR];
+        double2 p[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            k[u] = make_int2(a.g.G, 0);
+            if (i < a.n) {
+                k[u] = a.key_rank[i];
+                if (a.spts) p[u] = a.pts[i];
+            }
+        }
+        int pos[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) pos[u] = k[u].x < a.g.G ? a.cell_start[k[u].x] + k[u].y : -1;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (pos[u] >= 0) {
+                a.perm[pos[u]] = i0 + u * T;
+                if (a.spts) a.spts[pos[u]] = p[u];
+            }
         }
     }
 }
@@ -213,6 +254,13 @@ static int stream_blocks(long long n, int per_block, int cap) {
     if (b < 1) b = 1;
     if (b > cap) b = cap;
     return (int)b;
+}
+
+// The scan alone (per-cell counts already in a.cnt): cell_start, work items
+// and totals.  Grid size depends only on G, so the launch can be replayed.
+cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
+    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch}, a.g.G,
+                    a.block_sums, a.totals, s);
 }
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s) {
@@ -262,22 +310,35 @@ __global__ void k_ring_next(const int *ring_off, int R, int *nxt) {
     }
 }
 
-// (hi, lo) FP32 split of each vertex: hi = fl32(x), lo = fl32(x - hi).
+// (hi, lo) FP32 split of each vertex, the same split the kernels apply to
+// points: hi = x truncated to FP32, lo = fl32(x - hi).
 __global__ void k_split(const double2 *v, int n, float4 *vs) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double2 p = v[i];
-        float xh = __double2float_rn(p.x), yh = __double2float_rn(p.y);
-        float xl = __double2float_rn(__dsub_rn(p.x, (double)xh));
-        float yl = __double2float_rn(__dsub_rn(p.y, (double)yh));
+        float xh, xl, yh, yl;
+        split_double(p.x, xh, xl);
+        split_double(p.y, yh, yl);
         vs[i] = make_float4(xh, yh, xl, yl);
     }
+}
+
+// FP32 frame origins: frame[k] = fl32(lo + k * w), k = 0..n-1.
+__global__ void k_frames(double lo, double w, int n, float *frame) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        frame[k] = __double2float_rn(__dadd_rn(lo, __dmul_rn((double)k, w)));
+}
+
+cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s) {
+    k_frames<<<(g.nx + 255) / 256, 256, 0, s>>>(g.x0, g.cw, g.nx, fx);
+    k_frames<<<(g.ny + 255) / 256, 256, 0, s>>>(g.y0, g.ch, g.ny, fy);
+    return cudaGetLastError();
 }
 
 // P2P segment table: for the segment that starts at vertex i of polyline l,
 // e = v[i+1] - v[i] and 1 / |e|^2 (0 for a zero-length segment, and for the
 // single vertex of a one-vertex polyline, which then acts as a point).
-__global__ void k_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
-                            float *inv32) {
+__global__ void k_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64,
+                            float4 *seg32) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
         int b = line_off[l], e = line_off[l + 1];
         for (int i = b; i < e; ++i) {
@@ -290,8 +351,7 @@ __global__ void k_seg_table(const double2 *v, const int *line_off, int L, double
             }
             e64[i] = make_double2(ex, ey);
             inv64[i] = inv;
-            e32[i] = make_float2(__double2float_rn(ex), __double2float_rn(ey));
-            inv32[i] = __double2float_rn(inv);
+            seg32[i] = make_float4(__double2float_rn(ex), __double2float_rn(ey), __double2float_rn(inv), 0.0f);
         }
     }
 }
@@ -408,9 +468,9 @@ cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s) {
     k_split<<<stream_blocks(n, 256, 4096), 256, 0, s>>>(v, n, vs);
     return cudaGetLastError();
 }
-cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float2 *e32,
-                             float *inv32, cudaStream_t s) {
-    k_seg_table<<<stream_blocks(L, 128, 4096), 128, 0, s>>>(v, line_off, L, e64, inv64, e32, inv32);
+cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float4 *seg32,
+                             cudaStream_t s) {
+    k_seg_table<<<stream_blocks(L, 128, 4096), 128, 0, s>>>(v, line_off, L, e64, inv64, seg32);
     return cudaGetLastError();
 }
 cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s) {

@@ -1,0 +1,102 @@
+// sj_host.hpp -- host-side internals shared by the C ABI translation units
+// (sj_api.cu, sj_engine.cu): the layer object, error reporting, device info
+// and the scratch carver.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "sj.h"
+#include "sj_internal.cuh"
+
+struct sj_layer {
+    int kind = 0;
+    int device = 0;
+    sj_grid grid{};
+    sj::GridDev g{};
+    int nobj = 0;
+    int V = 0;
+    int64_t R = 0;
+    double D = 0.0;
+    int64_t M = 0;
+    float eps_abs = 0.0f;
+    double2 *verts = nullptr;
+    float4 *vsplit = nullptr;
+    int *obj_voff = nullptr;
+    int *nxt = nullptr;
+    int *ring_off = nullptr;
+    int *poly_ring_off = nullptr;
+    double2 *seg_e64 = nullptr;
+    double *seg_inv64 = nullptr;
+    float4 *seg32 = nullptr;   // (fl32(ex), fl32(ey), fl32(1 / |e|^2), 0)
+    sj::Box *mbb = nullptr;
+    int *cand_start = nullptr;
+    int *cand_ids = nullptr;
+    unsigned long long *stats = nullptr;
+    unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
+    float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins
+    double xmax = 0.0;                         // largest |coordinate| of the grid box
+    float Df = 0.0f, Ddn = 0.0f, Dup = 0.0f;   // FP32 forms of D (nearest, rounded down, rounded up)
+    mutable std::atomic<long long> joins{0};
+    mutable std::atomic<long long> points{0};
+    // SJ_FLAG_TIME_REFINE: event pairs recorded around refinement launches,
+    // resolved (and destroyed) by sj_layer_get_stats.
+    mutable std::mutex ev_mu;
+    mutable std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    mutable double refine_ms = 0.0;
+    mutable long long refine_launches = 0;
+};
+
+namespace sj {
+
+// Per-device launch facts, filled on first use.
+struct DevInfo {
+    int sms = 0;
+    int pip_bps[2] = {0, 0};
+    int p2p_bps[2] = {0, 0};
+    bool init = false;
+};
+
+sj_status fail(sj_status st, const std::string &msg);
+sj_status cuda_fail(cudaError_t e, const char *what);
+sj_status device_info(int dev, DevInfo **out);
+void fill_refine(const sj_layer *L, RefineArgs &ra);
+
+inline bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Scratch carved from one allocation, 256-byte aligned pieces.
+struct Scratch {
+    char *base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T *take(size_t n) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = (T *)(base + off);
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+template <class F>
+size_t measure(F f) {
+    Scratch s;
+    f(s);
+    return s.off + 256;
+}
+
+// Launchers shared across files.
+cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s);
+
+}  // namespace sj
+
+#define CUDA_TRY(x)                                          \
+    do {                                                     \
+        cudaError_t e_ = (x);                                \
+        if (e_ != cudaSuccess) return sj::cuda_fail(e_, #x); \
+    } while (0)

@@ -52,6 +52,39 @@ __device__ __forceinline__ float approx_float(double v) {
     return __uint_as_float(bits | (hi & 0x80000000u));
 }
 
+// Split a finite double v into FP32 hi + lo with integer and FP32 operations
+// only: hi = v truncated toward zero to FP32 (a monotone map), lo = fl32(v - hi)
+// (the 29 mantissa bits the truncation drops, converted and scaled by a power
+// of two).  |v - hi| < ulp32(hi) <= 2^-23 |v|; magnitudes below 2^-126 give
+// hi = lo = 0 and magnitudes beyond the FP32 range are clamped (callers keep
+// coordinates below 1e30).
+__device__ __forceinline__ void split_double(double v, float &hi, float &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    hi = approx_float(v);
+    const int pe = (int)((b >> 52) & 0x7ff) - 948;   // FP32 biased exponent of 2^(e - 52)
+    const float scale = (pe >= 1 && pe <= 254) ? __int_as_float(pe << 23) : 0.0f;
+    const float l = __uint2float_rn((unsigned)(b & 0x1fffffffULL)) * scale;
+    lo = (b >> 63) ? -l : l;
+}
+
+// Cell-relative FP32 coordinate (hi - origin) + lo of a split value.
+__device__ __forceinline__ float rel_coord(float hi, float lo, float origin) {
+    return __fadd_rn(__fsub_rn(hi, origin), lo);
+}
+
+// Bit pattern of the double equal to a float (exact widening) with integer
+// operations only; finite normal or zero inputs, infinities kept.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xff, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0) bits = s;                                        // zero (FP32 subnormals flushed)
+    else if (e == 0xff) bits = s | 0x7ff0000000000000ULL | ((unsigned long long)m << 29);
+    else bits = s | ((unsigned long long)(e + 896) << 52) | ((unsigned long long)m << 29);
+    return __longlong_as_double((long long)bits);
+}
+
 // Cell index along one axis by threshold table: keys[k] is the order key of the
 // smallest double whose cell, floor(fl(fl(v - lo) / w)), is >= k, so the cell
 // of v is the k with keys[k] <= key(v) < keys[k + 1] (exactly the FP64 rule:
@@ -88,13 +121,11 @@ __device__ __forceinline__ int clamped_axis(double v, double lo, double w, int n
     return (int)f;
 }
 
-// FP32-representable frame origin of cell c: the lower-left corner rounded to
-// FP32 (stored as a double so that FP64 code can use it exactly).
-__device__ __forceinline__ double2 cell_frame(const GridDev &g, int c) {
-    int iy = c / g.nx, ix = c - iy * g.nx;
-    double ox = __dadd_rn(g.x0, __dmul_rn((double)ix, g.cw));
-    double oy = __dadd_rn(g.y0, __dmul_rn((double)iy, g.ch));
-    return make_double2((double)__double2float_rn(ox), (double)__double2float_rn(oy));
+// FP32 frame origin of cell c: the lower-left corner x0 + ix * cw rounded to
+// FP32, read from per-axis tables built with the layer (frame_x[nx], frame_y[ny]).
+__device__ __forceinline__ float2 cell_frame(const float *fx, const float *fy, int nx, int c) {
+    const int iy = c / nx;
+    return make_float2(fx[c - iy * nx], fy[iy]);
 }
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
@@ -123,7 +154,7 @@ struct Box {
 enum { KIND_PIP = 0, KIND_P2P = 1 };
 
 // Per-layer device counters (index into sj_run_stats order after `joins`).
-enum { ST_POINTS = 0, ST_ITEMS, ST_PAIRS, ST_TESTS, ST_FALLBACK, ST_HITS, ST_N };
+enum { ST_POINTS = 0, ST_ITEMS, ST_PAIRS, ST_TESTS, ST_FALLBACK, ST_HITS, ST_ALGO, ST_N };
 
 // Arguments of the refinement kernels.
 struct RefineArgs {
@@ -141,13 +172,18 @@ struct RefineArgs {
     const float4 *vsplit;    // [V] (fl32(x), fl32(y), fl32(x - fl32(x)), fl32(y - fl32(y)))
     const double2 *seg_e64;  // P2P: [V] b - a of the segment starting at vertex i
     const double *seg_inv64; // P2P: [V] 1 / |b - a|^2 (0 for a degenerate segment)
-    const float2 *seg_e32;   // P2P: fl32 of seg_e64
-    const float *seg_inv32;  // P2P: fl32 of seg_inv64
+    const float4 *seg32;     // P2P: (fl32(ex), fl32(ey), fl32(1 / |e|^2), 0)
     double D;                // P2P window
-    float eps_abs;           // absolute term of the vertex rounding bound
+    float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
+    float Df;                // D rounded to FP32 (staging prune)
+    float eps_abs;           // absolute term of the split-coordinate rounding bound
+    const float *frame_x;    // [nx] FP32 cell frame origins along x
+    const float *frame_y;    // [ny]
     int ch;                  // points per work item
     int *out_id;
     double *out_d;
+    int *res_id;             // when set: results in sorted order for every slot
+    double *res_d;           //   (hits and misses); out_id / perm unused
     int2 *fb;                // P2P FP32X: points to redo in FP64 (sorted slot, cell)
     int *n_fb;
     unsigned long long *stats;

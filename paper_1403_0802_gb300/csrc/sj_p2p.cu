@@ -2,18 +2,23 @@
 // item, the candidate polyline at the smallest distance, accepted when the
 // distance is within the window D.
 //
-// Work decomposition: one warp per (cell, point-chunk) item.  The warp first
-// reads the metadata of up to 32 candidate polylines at once (one per lane),
-// warp-scans their segment counts, and stages the concatenated segments of
-// all of them in shared memory in one strided pass (start point a, direction
-// e = b - a, 1 / |e|^2, polyline id) -- so the L2 round trips of different
-// candidates overlap instead of forming a chain per candidate.  It then splits
-// its lanes into point groups of SG lanes (SG chosen so that np points x S
-// segments fill the warp); each lane strides over the segments keeping a
-// running "top-2" -- the best (squared distance, polyline) and the best
-// distance of any *other* polyline -- and the SG lanes of a group fold their
-// top-2s with shuffles (the cross-lane min of the vertex-per-lane alternative
-// of Sec. III.B).  Per point the result lives in shared memory across chunks.
+// Work decomposition: one warp per (cell, point-chunk) item.
+//   1. The item's points are converted to cell-relative coordinates and their
+//      bounding box is reduced across the warp.
+//   2. Candidate polylines are taken 32 at a time (one per lane): their vertex
+//      ranges are read in parallel and their segment counts warp-scanned.
+//   3. Staging: the concatenated segments of the group are read 32 at a time;
+//      a segment whose bounding box is farther than D (plus a rounding slack)
+//      from the points' box cannot be within D of any point of the item and is
+//      dropped (exact: it cannot change any result); the others are compacted
+//      into shared memory (a, e = b - a, 1 / |e|^2, polyline id) with a ballot.
+//   4. Whenever the staging area fills, the warp splits its lanes into point
+//      groups of SG lanes (SG chosen so that np points x staged segments fill
+//      the warp); each lane strides over the staged segments keeping a running
+//      "top-2" -- the best (squared distance, polyline) and the best distance
+//      of any other polyline -- and the SG lanes of a group fold their top-2s
+//      with shuffles (the cross-lane min of the vertex-per-lane alternative of
+//      Sec. III.B); the fold is merged into the point's state in shared memory.
 //
 // The point-to-segment distance is the two-case distance of Fig. 2 written as
 // the clamped projection: t = clamp(((p - a) . e) / |e|^2, 0, 1) and
@@ -24,12 +29,13 @@
 //   FP64   -- the formula in FP64 (ties of equal squared distance go to the
 //             smaller id); agrees with the two-case FP64 evaluation to a few
 //             ulps of the coordinates' magnitude.
-//   FP32X  -- cell-relative FP32 coordinates; every (point, polyline) distance
-//             carries the bound E = 64 u max|coordinate| + 4 eps (u = 2^-24,
-//             max over the point and every staged vertex of the item).  A
-//             point is final only when its best polyline is ahead of the
-//             runner-up by more than 2E and its distance differs from D by
-//             more than E; otherwise it is queued and redone in FP64
+//   FP32X  -- cell-relative FP32 coordinates from the (hi, lo) split of the FP64
+//             inputs; no FP64 instruction is executed.  Every (point, polyline)
+//             distance carries the bound E = 64 u M + 4 eps (u = 2^-24, M the
+//             largest |coordinate| of the point and of the item's staged
+//             segments).  A point is final only when its best polyline is ahead
+//             of the runner-up by more than 2E and its distance differs from D
+//             by more than E; otherwise it is queued and redone in FP64
 //             (k_p2p_recheck), so ids agree with FP64 up to exact ties.
 #include <cuda_runtime.h>
 
@@ -41,25 +47,33 @@ namespace sj {
 
 constexpr int P2P_WARPS = 4;
 
-template <bool FP32>
-struct P2PCfg {
-    using T = float;
-    static constexpr int SMAX = 512;   // staged segments per chunk per warp
-};
-template <>
-struct P2PCfg<false> {
-    using T = double;
-    static constexpr int SMAX = 256;
+struct alignas(16) Seg64 {
+    double ax, ay, ex, ey;
 };
 
 template <bool FP32>
-struct P2PSmem {
-    using T = typename P2PCfg<FP32>::T;
-    static constexpr int SMAX = P2PCfg<FP32>::SMAX;
-    T ax[SMAX], ay[SMAX], ex[SMAX], ey[SMAX], inv[SMAX];
+struct P2PSmem;
+
+template <>
+struct P2PSmem<true> {
+    static constexpr int SMAX = 128;
+    float4 seg[SMAX];        // cell-relative a (x, y) and e (x, y)
+    float2 si[SMAX];         // (1 / |e|^2, polyline id as bits)
+    int coff[33], cid[32], cvb[32];
+    float2 pt[MAX_CH];
+    float b1[MAX_CH], b2[MAX_CH];
+    int i1[MAX_CH];
+};
+
+template <>
+struct P2PSmem<false> {
+    static constexpr int SMAX = 128;
+    Seg64 seg[SMAX];
+    double inv[SMAX];
     int sid[SMAX];
-    int coff[33], cid[32], cvb[32];   // candidate group: segment offsets, ids, first vertices
-    T px[MAX_CH], py[MAX_CH], b1[MAX_CH], b2[MAX_CH];
+    int coff[33], cid[32], cvb[32];
+    double2 pt[MAX_CH];
+    double b1[MAX_CH], b2[MAX_CH];
     int i1[MAX_CH];
 };
 
@@ -92,13 +106,11 @@ struct Best {
 template <bool FP32, typename T>
 __device__ __forceinline__ void consider(Best<T> &s, T d, int l) {
     if constexpr (FP32) {
-        if (d < s.b1) {
-            s.b2 = (l != s.i1) ? s.b1 : s.b2;
-            s.b1 = d;
-            s.i1 = l;
-        } else if (d < s.b2 && l != s.i1) {
-            s.b2 = d;
-        }
+        const bool lt = d < s.b1, same = (l == s.i1);
+        const T nb2 = lt ? (same ? s.b2 : s.b1) : ((!same && d < s.b2) ? d : s.b2);
+        s.b1 = lt ? d : s.b1;
+        s.i1 = lt ? l : s.i1;
+        s.b2 = nb2;
     } else {
         if (d < s.b1 || (d == s.b1 && l < s.i1)) {
             s.b1 = d;
@@ -134,16 +146,68 @@ __device__ __forceinline__ Best<T> shfl_best(const Best<T> &s, int o) {
     return r;
 }
 
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+}
+
+// Refine the staged segments [0, ns) for the item's np points.
+template <bool FP32>
+__device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, int lane) {
+    using T = typename std::conditional<FP32, float, double>::type;
+    const T INF = (T)__longlong_as_double(0x7ff0000000000000LL);
+    const int sg = choose_group(np, ns, 2);
+    const int lg = __ffs(sg) - 1, pg = 32 >> lg;
+    const int sub = lane & (sg - 1), grp = lane >> lg;
+    for (int q0 = 0; q0 < np; q0 += pg) {
+        const int q = q0 + grp;
+        Best<T> st{INF, INF, -1};
+        if (q < np) {
+            if constexpr (FP32) {
+                const float2 p = s.pt[q];
+#pragma unroll 2
+                for (int t = sub; t < ns; t += sg) {
+                    const float4 g = s.seg[t];
+                    const float2 h = s.si[t];
+                    consider<true>(st, seg_d2(p.x, p.y, g.x, g.y, g.z, g.w, h.x), __float_as_int(h.y));
+                }
+            } else {
+                const double2 p = s.pt[q];
+                for (int t = sub; t < ns; t += sg) {
+                    const Seg64 g = s.seg[t];
+                    consider<false>(st, seg_d2(p.x, p.y, g.ax, g.ay, g.ex, g.ey, s.inv[t]), s.sid[t]);
+                }
+            }
+        }
+        for (int o = sg >> 1; o > 0; o >>= 1) st = merge<FP32>(st, shfl_best<FP32>(st, o));
+        if (sub == 0 && q < np) {
+            Best<T> cur{s.b1[q], s.b2[q], s.i1[q]};
+            cur = merge<FP32>(cur, st);
+            s.b1[q] = cur.b1;
+            s.b2[q] = cur.b2;
+            s.i1[q] = cur.i1;
+        }
+    }
+}
+
 template <bool FP32>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
-    using T = typename P2PCfg<FP32>::T;
-    constexpr int SMAX = P2PCfg<FP32>::SMAX;
+    using T = typename std::conditional<FP32, float, double>::type;
+    constexpr int SMAX = P2PSmem<FP32>::SMAX;
     extern __shared__ __align__(16) unsigned char p2p_smem_raw[];
     const int lane = lane_id(), w = threadIdx.x >> 5;
     P2PSmem<FP32> &s = reinterpret_cast<P2PSmem<FP32> *>(p2p_smem_raw)[w];
     const int n_items = *a.n_items;
     const T INF = (T)__longlong_as_double(0x7ff0000000000000LL);
-    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0;
+    const float FINF = __int_as_float(0x7f800000);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0;
     unsigned c_fb = 0, c_hits = 0;
 
     for (int it = blockIdx.x * P2P_WARPS + w; it < n_items; it += gridDim.x * P2P_WARPS) {
@@ -153,28 +217,33 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         const int j0 = a.cell_start[c] + item.y;
         const int np = min(a.ch, a.cell_start[c + 1] - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
-        double2 fr = make_double2(0.0, 0.0);
-        if (FP32) fr = cell_frame(a.g, c);
-        const float fox = (float)fr.x, foy = (float)fr.y;
+        const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
+        // 1. points: cell-relative FP32 coordinates, their box and magnitude
+        float bxlo = FINF, bxhi = -FINF, bylo = FINF, byhi = -FINF, pmag = 0.0f;
         for (int q = lane; q < np; q += 32) {
-            double2 p = a.spts[j0 + q];
-            if constexpr (FP32) {
-                s.px[q] = __double2float_rn(__dsub_rn(p.x, fr.x));
-                s.py[q] = __double2float_rn(__dsub_rn(p.y, fr.y));
-            } else {
-                s.px[q] = p.x;
-                s.py[q] = p.y;
-            }
+            const double2 p = a.spts[j0 + q];
+            float hx, lx, hy, ly;
+            split_double(p.x, hx, lx);
+            split_double(p.y, hy, ly);
+            const float rx = rel_coord(hx, lx, fo.x), ry = rel_coord(hy, ly, fo.y);
+            if constexpr (FP32) s.pt[q] = make_float2(rx, ry);
+            else s.pt[q] = p;
             s.b1[q] = INF;
             s.b2[q] = INF;
             s.i1[q] = -1;
+            bxlo = fminf(bxlo, rx); bxhi = fmaxf(bxhi, rx);
+            bylo = fminf(bylo, ry); byhi = fmaxf(byhi, ry);
+            pmag = fmaxf(pmag, fmaxf(fabsf(rx), fabsf(ry)));
         }
-        float mag = 0.0f;   // FP32X: largest |cell-relative coordinate| staged for this item
+        bxlo = warp_min(bxlo); bylo = warp_min(bylo);
+        bxhi = warp_max(bxhi); byhi = warp_max(byhi);
+        pmag = warp_max(pmag);
+        float mag = pmag;   // FP32X: largest |cell-relative coordinate| refined for this item
         c_pairs += (unsigned long long)np * (unsigned long long)(k1 - k0);
 
         for (int kg = k0; kg < k1; kg += 32) {
-            // candidate group: one polyline per lane, segment counts scanned
+            // 2. candidate group: one polyline per lane, segment counts scanned
             const int nc = min(32, k1 - kg);
             int lid = 0, vb = 0, nseg = 0;
             if (lane < nc) {
@@ -190,7 +259,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                 if (lane >= o) incl += v;
             }
             const int S = __shfl_sync(FULL, incl, 31);
-            __syncwarp();   // previous chunk's readers are done with the staging area
+            __syncwarp();
             if (lane < nc) {
                 s.coff[lane] = incl - nseg;
                 s.cid[lane] = lid;
@@ -198,85 +267,100 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             }
             if (lane == 0) s.coff[nc] = S;
             __syncwarp();
-            c_tests += (unsigned long long)np * (unsigned long long)S;
 
-            for (int s0 = 0; s0 < S; s0 += SMAX) {
-                const int ns = min(SMAX, S - s0);
-                for (int t = lane; t < ns; t += 32) {
-                    const int g = s0 + t;
-                    int lo = 0, hi = nc;   // coff[lo] <= g < coff[hi]
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s.coff[mid] <= g) lo = mid; else hi = mid;
-                    }
-                    const int i = s.cvb[lo] + (g - s.coff[lo]);
-                    s.sid[t] = s.cid[lo];
+            // 3. staging with the exact distance prune, 4. refinement when full
+            c_algo += (unsigned long long)np * (unsigned long long)S;
+            int nst = 0, kw = 0;
+            for (int base = 0; base < S; base += 32) {
+                const int g = base + lane;
+                bool keep = false;
+                int i = 0, sid = 0;
+                float ax = 0.0f, ay = 0.0f, ex = 0.0f, ey = 0.0f, inv = 0.0f, smag = 0.0f;
+                if (g < S) {
+                    while (s.coff[kw + 1] <= g) ++kw;   // candidate of segment g (g grows by 32)
+                    i = s.cvb[kw] + (g - s.coff[kw]);
+                    sid = s.cid[kw];
+                    const float4 v = a.vsplit[i];
+                    const float4 e = a.seg32[i];
+                    ax = rel_coord(v.x, v.z, fo.x);
+                    ay = rel_coord(v.y, v.w, fo.y);
+                    ex = e.x;
+                    ey = e.y;
+                    inv = e.z;
+                    const float bx = ax + ex, by = ay + ey;
+                    const float gx = fmaxf(0.0f, fmaxf(fminf(ax, bx) - bxhi, bxlo - fmaxf(ax, bx)));
+                    const float gy = fmaxf(0.0f, fmaxf(fminf(ay, by) - byhi, bylo - fmaxf(ay, by)));
+                    smag = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by)));
+                    // rounding slack of the relative coordinates of both boxes (far above it)
+                    const float lim = a.Df * (1.0f + 1e-6f) + 8.0f * U32 * (smag + pmag) + 8.0f * a.eps_abs;
+                    keep = gx * gx + gy * gy <= lim * lim * (1.0f + 8.0f * U32);
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int pos = nst + __popc(bal & lt_mask);
                     if constexpr (FP32) {
-                        const float4 v = a.vsplit[i];
-                        const float2 e = a.seg_e32[i];
-                        const float ax = __fadd_rn(__fsub_rn(v.x, fox), v.z);
-                        const float ay = __fadd_rn(__fsub_rn(v.y, foy), v.w);
-                        s.ax[t] = ax; s.ay[t] = ay; s.ex[t] = e.x; s.ey[t] = e.y;
-                        s.inv[t] = a.seg_inv32[i];
-                        mag = fmaxf(mag, fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(ax + e.x), fabsf(ay + e.y))));
+                        s.seg[pos] = make_float4(ax, ay, ex, ey);
+                        s.si[pos] = make_float2(inv, __int_as_float(sid));
+                        mag = fmaxf(mag, smag);
                     } else {
-                        const double2 v = a.verts[i];
-                        const double2 e = a.seg_e64[i];
-                        s.ax[t] = v.x; s.ay[t] = v.y; s.ex[t] = e.x; s.ey[t] = e.y;
-                        s.inv[t] = a.seg_inv64[i];
+                        const double2 v = a.verts[i], e = a.seg_e64[i];
+                        s.seg[pos] = Seg64{v.x, v.y, e.x, e.y};
+                        s.inv[pos] = a.seg_inv64[i];
+                        s.sid[pos] = sid;
                     }
                 }
-                __syncwarp();
-                const int sg = choose_group(np, ns, 2);
-                const int lg = __ffs(sg) - 1, pg = 32 >> lg;
-                const int sub = lane & (sg - 1), grp = lane >> lg;
-                for (int q0 = 0; q0 < np; q0 += pg) {
-                    const int q = q0 + grp;
-                    Best<T> st{INF, INF, -1};
-                    if (q < np) {
-                        const T px = s.px[q], py = s.py[q];
-                        for (int t = sub; t < ns; t += sg)
-                            consider<FP32>(st, seg_d2(px, py, s.ax[t], s.ay[t], s.ex[t], s.ey[t], s.inv[t]), s.sid[t]);
+                nst += __popc(bal);
+                if (nst > SMAX - 32 || base + 32 >= S) {
+                    __syncwarp();
+                    if (nst > 0) {
+                        p2p_compute<FP32>(s, np, nst, lane);
+                        c_tests += (unsigned long long)np * (unsigned long long)nst;
                     }
-                    for (int o = sg >> 1; o > 0; o >>= 1) st = merge<FP32>(st, shfl_best<FP32>(st, o));
-                    if (sub == 0 && q < np) {
-                        Best<T> cur{s.b1[q], s.b2[q], s.i1[q]};
-                        cur = merge<FP32>(cur, st);
-                        s.b1[q] = cur.b1; s.b2[q] = cur.b2; s.i1[q] = cur.i1;
-                    }
+                    __syncwarp();
+                    nst = 0;
                 }
-                __syncwarp();
             }
         }
-        if constexpr (FP32) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) mag = fmaxf(mag, __shfl_xor_sync(FULL, mag, o));
-        }
+        if constexpr (FP32) mag = warp_max(mag);
         for (int q = lane; q < np; q += 32) {
             const int id = s.i1[q];
-            if (id < 0) continue;
-            const double d = (double)sqrt(s.b1[q]);
-            if constexpr (FP32) {
-                const double e = (double)fmaf(64.0f * U32, fmaxf(mag, fmaxf(fabsf(s.px[q]), fabsf(s.py[q]))),
-                                              4.0f * a.eps_abs);
-                const double d2 = (double)sqrtf(s.b2[q]);
-                const double tiny = 1e-12 * (a.D + 1.0);
-                if (d - e > a.D + tiny) continue;                      // certainly outside the window
-                const bool in_window = d + e < a.D - tiny;
-                const bool separated = d2 - d > 2.0 * e + tiny;         // d2 = inf: no runner-up
-                if (!(in_window && separated)) {
-                    const int slot = atomicAdd(a.n_fb, 1);
-                    a.fb[slot] = make_int2(j0 + q, c);
-                    ++c_fb;
-                    continue;
+            int out = -1;
+            double dd = __longlong_as_double(0x7ff0000000000000LL);
+            if (id >= 0) {
+                if constexpr (FP32) {
+                    const float d = sqrtf(s.b1[q]), d2 = sqrtf(s.b2[q]);
+                    const float2 p = s.pt[q];
+                    const float e = fmaf(64.0f * U32, fmaxf(mag, fmaxf(fabsf(p.x), fabsf(p.y))), 4.0f * a.eps_abs) *
+                                    (1.0f + 8.0f * U32);
+                    if (!((d - e) * (1.0f - 4.0f * U32) > a.Dup)) {                  // not certainly outside D
+                        const bool in_window = (d + e) * (1.0f + 4.0f * U32) < a.Ddn;
+                        const bool separated = (d2 - d) * (1.0f - 4.0f * U32) > 2.0f * e * (1.0f + 4.0f * U32);
+                        if (!(in_window && separated)) {                              // redo in FP64
+                            const int slot = atomicAdd(a.n_fb, 1);
+                            a.fb[slot] = make_int2(j0 + q, c);
+                            ++c_fb;
+                            continue;
+                        }
+                        out = id;
+                        dd = widen(d);
+                    }
+                } else {
+                    const double d = sqrt(s.b1[q]);
+                    if (d <= a.D) {
+                        out = id;
+                        dd = d;
+                    }
                 }
-            } else {
-                if (!(d <= a.D)) continue;
             }
-            const int i = a.perm[j0 + q];
-            a.out_id[i] = id;
-            if (a.out_d) a.out_d[i] = d;
-            ++c_hits;
+            if (a.res_id) {
+                a.res_id[j0 + q] = out;
+                if (a.res_d) a.res_d[j0 + q] = dd;
+            } else if (out >= 0) {
+                const int i = a.perm[j0 + q];
+                a.out_id[i] = out;
+                if (a.out_d) a.out_d[i] = dd;
+            }
+            if (out >= 0) ++c_hits;
         }
         __syncwarp();
     }
@@ -287,6 +371,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             atomicAdd(&a.stats[ST_ITEMS], c_items);
             atomicAdd(&a.stats[ST_PAIRS], c_pairs);
             atomicAdd(&a.stats[ST_TESTS], c_tests);
+            atomicAdd(&a.stats[ST_ALGO], c_algo);
             atomicAdd(&a.stats[ST_FALLBACK], (unsigned long long)c_fb);
             atomicAdd(&a.stats[ST_HITS], (unsigned long long)c_hits);
         }
@@ -323,11 +408,17 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
             const double d = sqrt(m);
             if (d < best) { best = d; bid = lid; }
         }
-        if (lane == 0 && bid >= 0 && best <= a.D) {
-            const int i = a.perm[j];
-            a.out_id[i] = bid;
-            if (a.out_d) a.out_d[i] = best;
-            ++c_hits;
+        const bool hit = bid >= 0 && best <= a.D;
+        if (lane == 0) {
+            if (a.res_id) {
+                a.res_id[j] = hit ? bid : -1;
+                if (a.res_d) a.res_d[j] = hit ? best : INF;
+            } else if (hit) {
+                const int i = a.perm[j];
+                a.out_id[i] = bid;
+                if (a.out_d) a.out_d[i] = best;
+            }
+            if (hit) ++c_hits;
         }
     }
     if (a.stats) {

@@ -1,25 +1,36 @@
 // sj_pip.cu -- PIP refinement (Sec. III.C, Fig. 3): ray-crossing parity of
 // each point of a work item against every ring of each candidate polygon of
-// its cell.
+// its cell; the result is the smallest candidate id with odd parity.
 //
 // Work decomposition (GB300 design, not the paper's block-per-cell mapping):
-// one warp per (cell, point-chunk) item.  For each candidate polygon, in id
-// order, the warp stages the polygon's edges in shared memory in chunks, then
-// splits its 32 lanes into point groups of SG lanes (SG chosen per chunk so
-// that np points x ne edges fill the warp); the lanes of a group stride over
-// the edges and a single ballot folds the groups' parities.  A point leaves
-// the candidate loop once a polygon contains it (ids are visited in
-// increasing order, so the first hit is the smallest id).
+// one warp per (cell, point-chunk) item.
+//   1. The item's points are loaded; the range [ymin, ymax] of their FP32
+//      y roundings is reduced across the warp.
+//   2. Candidate polygons are taken 32 at a time (one per lane, in id order):
+//      vertex ranges read in parallel, edge counts warp-scanned.
+//   3. Staging: the concatenated edges of the group are read 32 at a time; an
+//      edge whose y-range lies strictly below ymin or strictly above ymax
+//      cannot straddle the horizontal line of any point of the item and is
+//      dropped (exact: its crossing count is 0 for every point; the test uses
+//      FP32 roundings that are monotone, with strict inequalities); the rest is
+//      compacted into shared memory with the lane's candidate index k.
+//   4. Whenever the staging area fills, the lanes split into point groups of
+//      SG lanes; each lane keeps a 32-bit parity mask (bit k = candidate k)
+//      over its strided share of the staged edges; the SG lanes XOR-fold their
+//      masks with shuffles, and the fold is XORed into the point's mask.
+//   After a group, a point's result is the lowest set bit of its mask (ids are
+//   sorted, so the smallest id); points with a result skip later groups.
 //
 // Two arithmetic forms:
 //   FP64   -- the crossing rule in FP64, each operation rounded, no FMA.
-//   FP32X  -- the straddle test on the FP32 roundings of y (monotone, so a
-//             strict FP32 inequality implies the FP64 one; equal values fall
-//             back), the orientation on cell-relative FP32 coordinates with a
-//             forward error bound (after Shewchuk's orient2d bound plus the
-//             input-rounding terms); a test whose |d| does not exceed the
-//             bound is redone in FP64 from the original vertices, so the
-//             result is the FP64 rule's, bit for bit.
+//   FP32X  -- no FP64 instruction in the common path: the straddle test on the
+//             FP32 truncations of y (monotone, so a strict FP32 inequality
+//             implies the FP64 one; equal values fall back), the orientation on
+//             cell-relative FP32 coordinates (from the (hi, lo) split of the
+//             inputs) with a forward error bound (Shewchuk's orient2d bound plus
+//             the input-rounding terms); a test whose |d| does not exceed the
+//             bound is redone in FP64 from the original vertices, so the result
+//             is the FP64 rule's, bit for bit.
 #include <cuda_runtime.h>
 
 #include "sj_internal.cuh"
@@ -27,25 +38,37 @@
 namespace sj {
 
 constexpr int PIP_WARPS = 4;
-constexpr int PIP_SMAX = 256;   // edges per staging chunk per warp
+
+struct alignas(16) Edge64 {
+    double ax, ay, bx, by;
+};
 
 template <bool FP32>
 struct PipSmem;
 
 template <>
-struct PipSmem<false> {
-    double ax[PIP_SMAX], ay[PIP_SMAX], bx[PIP_SMAX], by[PIP_SMAX];
-    double px[MAX_CH], py[MAX_CH];
-    int found[MAX_CH], par[MAX_CH];
+struct PipSmem<true> {
+    static constexpr int SMAX = 256;
+    float2 yh[SMAX];          // FP32 truncated y of the edge's two ends
+    float4 rel[SMAX];         // cell-relative (ax, ay, bx, by)
+    int vi[SMAX];             // global index of the edge's first end
+    unsigned char kk[SMAX];   // candidate index within the group
+    int coff[33], cid[32], cvb[32];
+    float2 pt[MAX_CH];
+    float pyh[MAX_CH];
+    int found[MAX_CH];
+    unsigned par[MAX_CH];
 };
 
 template <>
-struct PipSmem<true> {
-    float2 yh[PIP_SMAX];    // fl32(y) of the edge's two ends
-    float4 rel[PIP_SMAX];   // cell-relative (ax, ay, bx, by)
-    int vi[PIP_SMAX];       // global index of the edge's first end
-    float px[MAX_CH], py[MAX_CH], pyh[MAX_CH];
-    int found[MAX_CH], par[MAX_CH];
+struct PipSmem<false> {
+    static constexpr int SMAX = 128;
+    Edge64 e[SMAX];
+    unsigned char kk[SMAX];
+    int coff[33], cid[32], cvb[32];
+    double2 pt[MAX_CH];
+    int found[MAX_CH];
+    unsigned par[MAX_CH];
 };
 
 // The crossing rule in FP64: straddle iff (a.y > p.y) != (b.y > p.y); with lo
@@ -68,24 +91,23 @@ __device__ __noinline__ int cross64_global(const RefineArgs &a, int i, int j) {
 }
 
 // Sign of the orientation d = A*B - C*D on cell-relative FP32 inputs, certified
-// against the FP64 rule.  Inputs: point (px, py) rounded once from FP64
-// (error <= KP * |coord|), ends (lx, ly), (hx, hy) from the split vertices
-// (error <= KV * |coord| + eps).  Returns false when |d| does not exceed the
-// bound E = errA + errIn + err64:
+// against the FP64 rule.  Every input coordinate c carries the rounding bound
+// KV |c| + eps of the (hi, lo) split.  Returns false when |d| does not exceed
+// E = errA + errIn + err64:
 //   errA  = 3.0001 u (|AB| + |CD|)          FP32 rounding of d (Shewchuk orient2d)
 //   errIn = first-order input perturbation plus cross terms, x (1 + 4u)
 //   err64 = 4e-16 (|A||B| + |C||D|)         FP64 rounding of the reference rule
 // E is inflated by (1 + 16u) for the FP32 evaluation of the bound itself.
 __device__ __forceinline__ bool orient32(float px, float py, float lx, float ly, float hx, float hy, float eps,
                                          bool &pos) {
-    const float KV = 2.0001f * U32, KP = 1.0001f * U32;
+    const float KV = 2.0001f * U32;
     float A = __fsub_rn(hx, lx), B = __fsub_rn(py, ly);
     float C = __fsub_rn(hy, ly), Dd = __fsub_rn(px, lx);
     float AB = __fmul_rn(A, B), CD = __fmul_rn(C, Dd);
     float d = __fsub_rn(AB, CD);
     float dhx = fmaf(KV, fabsf(hx), eps), dhy = fmaf(KV, fabsf(hy), eps);
     float dlx = fmaf(KV, fabsf(lx), eps), dly = fmaf(KV, fabsf(ly), eps);
-    float dpx = KP * fabsf(px), dpy = KP * fabsf(py);
+    float dpx = fmaf(KV, fabsf(px), eps), dpy = fmaf(KV, fabsf(py), eps);
     float dA = dhx + dlx, dB = dpy + dly, dC = dhy + dly, dD = dpx + dlx;
     float aA = fabsf(A), aB = fabsf(B), aC = fabsf(C), aD = fabsf(Dd);
     float errIn = (dA * aB + aA * dB + dA * dB + dC * aD + aC * dD + dC * dD) * (1.0f + 4.0f * U32);
@@ -96,14 +118,72 @@ __device__ __forceinline__ bool orient32(float px, float py, float lx, float ly,
     return fabsf(d) > E;
 }
 
+// Parity masks of the staged edges [0, ns) for the item's pending points.
+template <bool FP32>
+__device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, const RefineArgs &a, int j0, int np,
+                                                          int ns, int lane, unsigned &c_fb) {
+    const int sg = choose_group(np, ns, 0);
+    const int lg = __ffs(sg) - 1, pg = 32 >> lg;
+    const int sub = lane & (sg - 1), grp = lane >> lg;
+    unsigned long long tests = 0;
+    for (int q0 = 0; q0 < np; q0 += pg) {
+        const int q = q0 + grp;
+        const bool act = q < np && s.found[q] < 0;
+        const unsigned actb = __ballot_sync(FULL, act && sub == 0);
+        if (!actb) continue;
+        tests += (unsigned long long)__popc(actb) * (unsigned long long)ns;
+        unsigned m = 0;
+        if (act) {
+            if constexpr (FP32) {
+                const float2 p = s.pt[q];
+                const float pyh = s.pyh[q];
+                for (int t = sub; t < ns; t += sg) {
+                    const float2 yh = s.yh[t];
+                    if ((yh.x == pyh) | (yh.y == pyh)) {   // FP32 y tie: decide in FP64
+                        m ^= (unsigned)cross64_global(a, s.vi[t], j0 + q) << s.kk[t];
+                        ++c_fb;
+                        continue;
+                    }
+                    const bool a_up = yh.x > pyh, b_up = yh.y > pyh;
+                    if (a_up == b_up) continue;
+                    const float4 r = s.rel[t];
+                    const float lx = a_up ? r.z : r.x, ly = a_up ? r.w : r.y;
+                    const float hx = a_up ? r.x : r.z, hy = a_up ? r.y : r.w;
+                    bool pos;
+                    int cr;
+                    if (orient32(p.x, p.y, lx, ly, hx, hy, a.eps_abs, pos)) {
+                        cr = (int)pos;
+                    } else {
+                        cr = cross64_global(a, s.vi[t], j0 + q);
+                        ++c_fb;
+                    }
+                    m ^= (unsigned)cr << s.kk[t];
+                }
+            } else {
+                const double2 p = s.pt[q];
+                for (int t = sub; t < ns; t += sg) {
+                    const Edge64 e = s.e[t];
+                    if (cross64(p.x, p.y, e.ax, e.ay, e.bx, e.by)) m ^= 1u << s.kk[t];
+                }
+            }
+        }
+        for (int o = sg >> 1; o > 0; o >>= 1) m ^= __shfl_xor_sync(FULL, m, o);
+        if (sub == 0 && act) s.par[q] ^= m;
+    }
+    return tests;
+}
+
 template <bool FP32>
 __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
-    __shared__ PipSmem<FP32> smem[PIP_WARPS];
+    constexpr int SMAX = PipSmem<FP32>::SMAX;
+    extern __shared__ __align__(16) unsigned char pip_smem_raw[];
     const int lane = lane_id(), w = threadIdx.x >> 5;
-    PipSmem<FP32> &s = smem[w];
+    PipSmem<FP32> &s = reinterpret_cast<PipSmem<FP32> *>(pip_smem_raw)[w];
     const int n_items = *a.n_items;
-    unsigned long long c_pairs = 0, c_tests = 0, c_fb = 0, c_hits = 0;
-    unsigned long long c_items = 0;
+    const float FINF = __int_as_float(0x7f800000);
+    const unsigned lt_mask = (1u << lane) - 1u;
+    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0;
+    unsigned c_fb = 0, c_hits = 0;
 
     for (int it = blockIdx.x * PIP_WARPS + w; it < n_items; it += gridDim.x * PIP_WARPS) {
         ++c_items;
@@ -111,137 +191,174 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
         const int c = item.x;
         const int j0 = a.cell_start[c] + item.y;
         const int np = min(a.ch, a.cell_start[c + 1] - j0);
-        double2 fr = make_double2(0.0, 0.0);
-        if (FP32) fr = cell_frame(a.g, c);
-        const float fox = (float)fr.x, foy = (float)fr.y;
+        const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
+        const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
+        // 1. points and the range of their FP32 y truncations
+        float ylo = FINF, yhi = -FINF;
         for (int q = lane; q < np; q += 32) {
-            double2 p = a.spts[j0 + q];
+            const double2 p = a.spts[j0 + q];
+            float hx, lx, hy, ly;
+            split_double(p.x, hx, lx);
+            split_double(p.y, hy, ly);
             if constexpr (FP32) {
-                s.px[q] = __double2float_rn(__dsub_rn(p.x, fr.x));
-                s.py[q] = __double2float_rn(__dsub_rn(p.y, fr.y));
-                s.pyh[q] = __double2float_rn(p.y);
+                s.pt[q] = make_float2(rel_coord(hx, lx, fo.x), rel_coord(hy, ly, fo.y));
+                s.pyh[q] = hy;
             } else {
-                s.px[q] = p.x;
-                s.py[q] = p.y;
+                s.pt[q] = p;
             }
             s.found[q] = -1;
-            s.par[q] = 0;
+            s.par[q] = 0u;
+            ylo = fminf(ylo, hy);
+            yhi = fmaxf(yhi, hy);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ylo = fminf(ylo, __shfl_xor_sync(FULL, ylo, o));
+            yhi = fmaxf(yhi, __shfl_xor_sync(FULL, yhi, o));
         }
         __syncwarp();
 
-        const int k1 = a.cand_start[c + 1];
-        for (int k = a.cand_start[c]; k < k1; ++k) {
+        for (int kg = k0; kg < k1; kg += 32) {
             int pending = 0;
             for (int q = lane; q < np; q += 32) pending += (s.found[q] < 0);
             pending = __reduce_add_sync(FULL, pending);
             if (pending == 0) break;
-            const int pid = a.cand_ids[k];
-            const int vb = a.obj_voff[pid], ne = a.obj_voff[pid + 1] - vb;
-            c_pairs += pending;
-            c_tests += (unsigned long long)pending * (unsigned long long)ne;
-
-            for (int e0 = 0; e0 < ne; e0 += PIP_SMAX) {
-                const int ns = min(PIP_SMAX, ne - e0);
-                for (int t = lane; t < ns; t += 32) {
-                    const int i = vb + e0 + t, j = a.nxt[i];
-                    if constexpr (FP32) {
-                        float4 va = a.vsplit[i], vc = a.vsplit[j];
-                        s.yh[t] = make_float2(va.y, vc.y);
-                        s.rel[t] = make_float4(__fadd_rn(__fsub_rn(va.x, fox), va.z), __fadd_rn(__fsub_rn(va.y, foy), va.w),
-                                               __fadd_rn(__fsub_rn(vc.x, fox), vc.z), __fadd_rn(__fsub_rn(vc.y, foy), vc.w));
-                        s.vi[t] = i;
-                    } else {
-                        double2 A = a.verts[i], B = a.verts[j];
-                        s.ax[t] = A.x; s.ay[t] = A.y; s.bx[t] = B.x; s.by[t] = B.y;
-                    }
-                }
-                __syncwarp();
-                const int sg = choose_group(np, ns, 0);
-                const int lg = __ffs(sg) - 1, pg = 32 >> lg;
-                const int sub = lane & (sg - 1), grp = lane >> lg;
-                const unsigned gmask = (sg == 32) ? FULL : (((1u << sg) - 1u) << (grp * sg));
-                for (int q0 = 0; q0 < np; q0 += pg) {
-                    const int q = q0 + grp;
-                    const bool act = q < np && s.found[q] < 0;
-                    if (!__any_sync(FULL, act)) continue;
-                    int odd = 0;
-                    if (act) {
-                        if constexpr (FP32) {
-                            const float px = s.px[q], py = s.py[q], pyh = s.pyh[q];
-                            for (int t = sub; t < ns; t += sg) {
-                                const float2 yh = s.yh[t];
-                                if ((yh.x == pyh) | (yh.y == pyh)) {   // FP32 y tie: decide in FP64
-                                    odd ^= cross64_global(a, s.vi[t], j0 + q);
-                                    ++c_fb;
-                                    continue;
-                                }
-                                const bool a_up = yh.x > pyh, b_up = yh.y > pyh;
-                                if (a_up == b_up) continue;
-                                const float4 r = s.rel[t];
-                                const float lx = a_up ? r.z : r.x, ly = a_up ? r.w : r.y;
-                                const float hx = a_up ? r.x : r.z, hy = a_up ? r.y : r.w;
-                                bool pos;
-                                if (orient32(px, py, lx, ly, hx, hy, a.eps_abs, pos)) {
-                                    odd ^= (int)pos;
-                                } else {
-                                    odd ^= cross64_global(a, s.vi[t], j0 + q);
-                                    ++c_fb;
-                                }
-                            }
-                        } else {
-                            const double px = s.px[q], py = s.py[q];
-                            for (int t = sub; t < ns; t += sg) odd ^= cross64(px, py, s.ax[t], s.ay[t], s.bx[t], s.by[t]);
-                        }
-                    }
-                    const unsigned bal = __ballot_sync(FULL, odd);
-                    if (sub == 0 && act) s.par[q] ^= (__popc(bal & gmask) & 1);
-                }
-                __syncwarp();
+            // 2. candidate group: one polygon per lane, edge counts scanned
+            const int nc = min(32, k1 - kg);
+            int pid = 0, vb = 0, ne = 0;
+            if (lane < nc) {
+                pid = a.cand_ids[kg + lane];
+                vb = a.obj_voff[pid];
+                ne = a.obj_voff[pid + 1] - vb;
             }
+            c_pairs += (unsigned long long)pending * (unsigned long long)nc;
+            int incl = ne;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += v;
+            }
+            const int E = __shfl_sync(FULL, incl, 31);
+            __syncwarp();
+            if (lane < nc) {
+                s.coff[lane] = incl - ne;
+                s.cid[lane] = pid;
+                s.cvb[lane] = vb;
+            }
+            if (lane == 0) s.coff[nc] = E;
+            __syncwarp();
+
+            // 3. staging with the exact y-range prune, 4. parity when full
+            c_algo += (unsigned long long)pending * (unsigned long long)E;
+            int nst = 0, kw = 0;
+            for (int base = 0; base < E; base += 32) {
+                const int g = base + lane;
+                bool keep = false;
+                int i = 0, j = 0, k = 0;
+                float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vc = va;
+                if (g < E) {
+                    while (s.coff[kw + 1] <= g) ++kw;   // candidate of edge g (g grows by 32)
+                    k = kw;
+                    i = s.cvb[kw] + (g - s.coff[kw]);
+                    j = a.nxt[i];
+                    va = a.vsplit[i];
+                    vc = a.vsplit[j];
+                    keep = !(fmaxf(va.y, vc.y) < ylo || fminf(va.y, vc.y) > yhi);
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep) {
+                    const int pos = nst + __popc(bal & lt_mask);
+                    if constexpr (FP32) {
+                        s.yh[pos] = make_float2(va.y, vc.y);
+                        s.rel[pos] = make_float4(rel_coord(va.x, va.z, fo.x), rel_coord(va.y, va.w, fo.y),
+                                                 rel_coord(vc.x, vc.z, fo.x), rel_coord(vc.y, vc.w, fo.y));
+                        s.vi[pos] = i;
+                    } else {
+                        const double2 A = a.verts[i], B = a.verts[j];
+                        s.e[pos] = Edge64{A.x, A.y, B.x, B.y};
+                    }
+                    s.kk[pos] = (unsigned char)k;
+                }
+                nst += __popc(bal);
+                if (nst > SMAX - 32 || base + 32 >= E) {
+                    __syncwarp();
+                    if (nst > 0) c_tests += pip_compute<FP32>(s, a, j0, np, nst, lane, c_fb);
+                    __syncwarp();
+                    nst = 0;
+                }
+            }
+            // smallest candidate with odd parity
             for (int q = lane; q < np; q += 32) {
-                if (s.found[q] < 0 && s.par[q]) s.found[q] = pid;
-                s.par[q] = 0;
+                const unsigned m = s.par[q];
+                if (s.found[q] < 0 && m) s.found[q] = s.cid[__ffs(m) - 1];
+                s.par[q] = 0u;
             }
             __syncwarp();
         }
         for (int q = lane; q < np; q += 32) {
             const int f = s.found[q];
-            if (f >= 0) {
-                a.out_id[a.perm[j0 + q]] = f;
-                ++c_hits;
-            }
+            if (a.res_id) a.res_id[j0 + q] = f;
+            else if (f >= 0) a.out_id[a.perm[j0 + q]] = f;
+            if (f >= 0) ++c_hits;
         }
         __syncwarp();
     }
     if (a.stats) {
-        c_fb = __reduce_add_sync(FULL, (unsigned)c_fb);
-        c_hits = __reduce_add_sync(FULL, (unsigned)c_hits);
+        c_fb = __reduce_add_sync(FULL, c_fb);
+        c_hits = __reduce_add_sync(FULL, c_hits);
+        const unsigned long long t = c_tests;   // per lane: tests of the rounds it led
         if (lane == 0) {
             atomicAdd(&a.stats[ST_ITEMS], c_items);
             atomicAdd(&a.stats[ST_PAIRS], c_pairs);
-            atomicAdd(&a.stats[ST_TESTS], c_tests);
-            atomicAdd(&a.stats[ST_FALLBACK], c_fb);
-            atomicAdd(&a.stats[ST_HITS], c_hits);
+            atomicAdd(&a.stats[ST_TESTS], t);
+            atomicAdd(&a.stats[ST_ALGO], c_algo);
+            atomicAdd(&a.stats[ST_FALLBACK], (unsigned long long)c_fb);
+            atomicAdd(&a.stats[ST_HITS], (unsigned long long)c_hits);
         }
     }
 }
 
+template <bool FP32>
+static size_t pip_smem_bytes() {
+    return sizeof(PipSmem<FP32>) * PIP_WARPS;
+}
+
+template <bool FP32>
+static cudaError_t pip_prepare() {
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(k_pip_refine<FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pip_smem_bytes<FP32>());
+        if (e != cudaSuccess) return e;
+        done = true;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
     (void)warps_per_block;
-    if (form == SJ_FP32X)
-        k_pip_refine<true><<<blocks, PIP_WARPS * 32, 0, s>>>(a);
-    else
-        k_pip_refine<false><<<blocks, PIP_WARPS * 32, 0, s>>>(a);
+    cudaError_t e;
+    if (form == SJ_FP32X) {
+        if ((e = pip_prepare<true>()) != cudaSuccess) return e;
+        k_pip_refine<true><<<blocks, PIP_WARPS * 32, pip_smem_bytes<true>(), s>>>(a);
+    } else {
+        if ((e = pip_prepare<false>()) != cudaSuccess) return e;
+        k_pip_refine<false><<<blocks, PIP_WARPS * 32, pip_smem_bytes<false>(), s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 int pip_blocks_per_sm(int form) {
     int n = 0;
-    if (form == SJ_FP32X)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<true>, PIP_WARPS * 32, 0);
-    else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<false>, PIP_WARPS * 32, 0);
+    if (form == SJ_FP32X) {
+        if (pip_prepare<true>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<true>, PIP_WARPS * 32, pip_smem_bytes<true>());
+    } else {
+        if (pip_prepare<false>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<false>, PIP_WARPS * 32,
+                                                      pip_smem_bytes<false>());
+    }
     return n > 0 ? n : 1;
 }
 

@@ -261,30 +261,37 @@ class Workload:
     meta: dict = field(default_factory=dict)
 
 
+def _point_rng(rng: np.random.Generator, seed: int, shard: int) -> np.random.Generator:
+    """Points of shard 0 continue the layer's generator; shard k > 0 (another
+    rank of a weak-scaling run) draws its own points from (seed, k), so every
+    rank joins different points against an identical layer."""
+    return rng if shard == 0 else np.random.default_rng((seed, shard))
+
+
 def pip_stars(n_points: int = 1_000_000, seed: int = SEED_BASE + 1, n_side: int = 32,
-              grid_n: int = 256) -> Workload:
+              grid_n: int = 256, shard: int = 0) -> Workload:
     """PIP, plain FP64 method: uniform points against a jittered lattice of
     1,024 star polygons (8-64 vertices), filter grid 256 x 256."""
     rng = np.random.default_rng(seed)
     layer = star_polygons(rng, n_side=n_side)
-    pts = points_uniform(n_points, rng)
+    pts = points_uniform(n_points, _point_rng(rng, seed, shard))
     return Workload("pip_1M_stars1024_grid256", "pip", pts, grid(grid_n), polygons=layer)
 
 
 def p2p_walks(n_points: int = 10_000_000, n_lines: int = 100_000, seed: int = SEED_BASE + 2,
-              D: float = 100.0, grid_n: int = 1024) -> Workload:
+              D: float = 100.0, grid_n: int = 1024, shard: int = 0) -> Workload:
     """P2P, plain FP64 method: mixture points against random-walk polylines with
     2-40 vertices, window D = 100 m, filter grid 1024 x 1024."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(2, 41, size=n_lines)
     layer = random_walks(rng, sizes)
-    pts = points_mixture(n_points, rng)
+    pts = points_mixture(n_points, _point_rng(rng, seed, shard))
     return Workload("p2p_10M_walks100k_D100_grid1024", "p2p", pts, grid(grid_n),
                     polylines=layer, D=float(D))
 
 
 def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE + 3,
-              grid_n: int = 1024) -> Workload:
+              grid_n: int = 1024, shard: int = 0) -> Workload:
     """PIP at scale: clustered points against a disjoint tiling.  Layer 1: 200 x 200
     tiles, side counts lognormal(median 2.6, sigma 1) capped at 1,250, three giant
     tiles (polygon median ~19, max ~5,000).  Layer 2: 140 x 100 tiles, side median
@@ -294,18 +301,18 @@ def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE
         P = tiling(rng, 200, 200, side_median=2.6, side_cap=1250, n_giant=3)
     else:
         P = tiling(rng, 140, 100, side_median=90.0, side_cap=25000, n_giant=3)
-    pts = points_mixture(n_points, np.random.default_rng(seed))
+    pts = points_mixture(n_points, _point_rng(np.random.default_rng(seed), seed, shard))
     return Workload(f"pip_{n_points}_tiles{P.n_polygons}_grid{grid_n}", "pip", pts, grid(grid_n), polygons=P)
 
 
 def p2p_walks_lognormal(n_points: int = 170_000_000, n_lines: int = 150_000,
                         seed: int = SEED_BASE + 4, D: float = 100.0,
-                        grid_n: int = 1024) -> Workload:
+                        grid_n: int = 1024, shard: int = 0) -> Workload:
     """P2P at scale: mixture points against random walks whose vertex counts are
     clamp(round(lognormal(ln 8, 0.8)), 2, 200)."""
     rng = np.random.default_rng(seed)
     sizes = np.clip(np.round(rng.lognormal(math.log(8.0), 0.8, size=n_lines)), 2, 200).astype(np.int64)
     layer = random_walks(rng, sizes)
-    pts = points_mixture(n_points, rng)
+    pts = points_mixture(n_points, _point_rng(rng, seed, shard))
     return Workload(f"p2p_{n_points}_walks{n_lines}_D{int(D)}_grid{grid_n}", "p2p", pts,
                     grid(grid_n), polylines=layer, D=float(D))

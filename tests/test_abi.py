@@ -68,7 +68,7 @@ def test_struct_layouts_match_header():
     from paper_1403_0802_gb300 import _lib
     assert C.sizeof(_lib.sj_grid) == 40
     assert C.sizeof(_lib.sj_opts) == 24
-    assert C.sizeof(_lib.sj_run_stats) == 72
+    assert C.sizeof(_lib.sj_run_stats) == 80
     assert C.sizeof(_lib.sj_layer_info) == 48
 
 
@@ -79,3 +79,8 @@ def test_binding_imports_without_a_gpu():
     assert api.FORMS == {"fp64": 0, "fp32x": 1}
     o = api._opts("fp32x", "persistent", 32, True)
     assert (o.form, o.launch, o.pts_per_item, o.flags) == (1, 1, 32, 1)
+
+
+def test_request_struct_layout():
+    from paper_1403_0802_gb300 import _lib
+    assert C.sizeof(_lib.sj_request) == 40

@@ -1,0 +1,89 @@
+"""Batched rounds (sj_engine_*): every request's result inside a round equals
+its result when joined alone, round after round (graph replay), for PIP and
+P2P requests mixed in one round, empty requests included."""
+import numpy as np
+import pytest
+
+from paper_1403_0802_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0802_gb300 import api, build
+    build.build()
+    wp = synth.pip_tiles(n_points=400_000, layer=1)
+    wl = synth.p2p_walks(n_points=400_000, n_lines=30_000)
+    pip = api.pip_layer(wp.polygons.verts, wp.polygons.ring_off, wp.polygons.poly_ring_off, wp.grid)
+    p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
+    yield api, pip, p2p, torch.as_tensor(wp.points, device="cuda"), torch.as_tensor(wl.points, device="cuda")
+    pip.close()
+    p2p.close()
+
+
+def make_requests(rng, pip, p2p, ptsP, ptsL, n):
+    reqs = []
+    for _ in range(n):
+        kind = rng.random() < 0.7
+        pool = ptsP if kind else ptsL
+        size = int(rng.choice([0, 1, 7, 1000, 20_000, 60_000]))
+        off = int(rng.integers(0, pool.shape[0] - size)) if size else 0
+        pts = pool[off:off + size].contiguous()
+        out_id = torch.full((size,), 99, dtype=torch.int32, device="cuda")
+        out_d = None if kind else torch.full((size,), -5.0, dtype=torch.float64, device="cuda")
+        reqs.append((pip if kind else p2p, pts, out_id, out_d))
+    return reqs
+
+
+@pytest.mark.parametrize("form", ["fp64", "fp32x"])
+@pytest.mark.parametrize("graph", [True, False])
+def test_rounds_match_single_joins(setup, form, graph):
+    api, pip, p2p, ptsP, ptsL = setup
+    rng = np.random.default_rng(3)
+    stream = torch.cuda.Stream()
+    with api.Engine(max_points=600_000, max_requests=64, form=form, graph=graph) as eng:
+        for rnd in range(4):
+            reqs = make_requests(rng, pip, p2p, ptsP, ptsL, int(rng.integers(1, 12)))
+            stream.wait_stream(torch.cuda.current_stream())     # inputs / outputs were made there
+            with torch.cuda.stream(stream):
+                eng.round(reqs, stream)
+            stream.synchronize()
+            for layer, pts, out_id, out_d in reqs:
+                if layer is pip:
+                    ref = api.pip_join(layer, pts, form=form) if pts.shape[0] else out_id
+                    torch.cuda.synchronize()
+                    assert torch.equal(out_id, ref), (rnd, pts.shape)
+                else:
+                    if pts.shape[0] == 0:
+                        continue
+                    rid, rd = api.p2p_join(layer, pts, form=form)
+                    torch.cuda.synchronize()
+                    a_id, a_d, b_id, b_d = (t.cpu().numpy() for t in (out_id, out_d, rid, rd))
+                    if form == "fp64":
+                        np.testing.assert_array_equal(a_id, b_id)
+                        np.testing.assert_array_equal(a_d, b_d)
+                    else:
+                        # certification may differ with the item's company: ids equal up to
+                        # FP64 near-ties, distances within the FP32X bound (a few mm here)
+                        assert (a_id == b_id).mean() > 0.9999
+                        both = (a_id >= 0) & (a_id == b_id)
+                        assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
+                        assert np.all(np.isinf(a_d[a_id < 0]))
+
+
+def test_round_limits(setup):
+    api, pip, p2p, ptsP, ptsL = setup
+    from paper_1403_0802_gb300._lib import SJError, SJ_ERR_INVALID
+    with api.Engine(max_points=1000, max_requests=2) as eng:
+        big = ptsP[:1001].contiguous()
+        with pytest.raises(SJError) as e:
+            eng.round([(pip, big, torch.empty(1001, dtype=torch.int32, device="cuda"), None)])
+        assert e.value.status == SJ_ERR_INVALID
+        small = ptsP[:10].contiguous()
+        outs = [torch.empty(10, dtype=torch.int32, device="cuda") for _ in range(3)]
+        with pytest.raises(SJError):
+            eng.round([(pip, small, o, None) for o in outs])         # 3 requests > max_requests

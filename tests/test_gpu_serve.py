@@ -1,0 +1,55 @@
+"""The continuous-batching serving loop: requests that arrive while others are
+on the GPU are admitted as memory frees up and joined in shared rounds, and
+each request's result is the same in the mix as alone (PIP ids bit-exact;
+P2P ids exact up to near-ties and distances within the FP32X bound)."""
+import numpy as np
+import pytest
+
+from paper_1403_0802_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def server():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0802_gb300 import api, build, serve
+    build.build()
+    wp = synth.pip_tiles(n_points=300_000, layer=1)
+    wl = synth.p2p_walks_lognormal(n_points=300_000, n_lines=20_000)
+    pip = api.pip_layer(wp.polygons.verts, wp.polygons.ring_off, wp.polygons.poly_ring_off, wp.grid)
+    p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
+    pool_p = torch.from_numpy(wp.points).pin_memory()
+    pool_l = torch.from_numpy(wl.points).pin_memory()
+    srv = serve.Server(pip, p2p, form="fp32x", round_points=400_000, max_requests=256,
+                       hbm_budget=40_000_000)
+    yield api, serve, srv, pool_p, pool_l
+    srv.close()
+    pip.close()
+    p2p.close()
+
+
+@pytest.mark.parametrize("mode", ["batched", "per_request"])
+def test_mix_equals_alone(server, mode):
+    api, serve, srv, pool_p, pool_l = server
+    reqs = serve.make_stream(80, rate_per_s=4000.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=100,
+                             size_max=60_000, seed=5)
+    stats = srv.run(reqs, mode=mode)
+    assert stats["requests"] == 80 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    if mode == "batched":
+        assert stats["rounds"] < 80            # requests really shared rounds
+    for r in reqs:
+        layer = srv.layers[r.kind]
+        pts = r.pts.cuda()
+        if r.kind == serve.PIP:
+            ref = api.pip_join(layer, pts, form=srv.form).cpu()
+            assert torch.equal(r.out_id, ref), r.rid
+        else:
+            rid, rd = api.p2p_join(layer, pts, form=srv.form)
+            a_id, a_d = r.out_id.numpy(), r.out_d.numpy()
+            b_id, b_d = rid.cpu().numpy(), rd.cpu().numpy()
+            assert (a_id == b_id).mean() > 0.999, r.rid
+            both = (a_id >= 0) & (a_id == b_id)
+            assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
