@@ -2,7 +2,7 @@
 
 Workloads (--workload):
   p2p    (default) P2P, 10,000,000 clustered points, 100,000 random-walk
-         polylines (2-40 vertices), window D = 100 m, grid 1024 x 1024
+         polylines (2-40 vertices), window D = 100 m, grid 512 x 512
   pip    PIP, 1,000,000 uniform points, 1,024 star polygons, grid 256 x 256
   pip3   PIP at scale, 100,000,000 clustered points against the 40,000-tile
          layer (--layer 1) or the 14,000-tile heavy-tail layer (--layer 2)
@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--D", type=float, default=100.0, help="p2p4: window")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count")
     ap.add_argument("--form", choices=["fp32x", "fp64"], default="fp32x")
+    ap.add_argument("--grid", type=int, default=0, help="filter grid cells per axis (0: the workload's)")
+    ap.add_argument("--ppi", type=int, default=0, help="points per work item, 1..128 (0: library default 64)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64, e2e and CPU comparison legs")
     return ap.parse_args()
@@ -63,14 +65,15 @@ def parse():
 def workload(args, rank: int = 0):
     from paper_1403_0802_gb300 import synth
     n = args.points or None
+    g = {"grid_n": args.grid} if getattr(args, "grid", 0) else {}
     if args.workload == "p2p":
-        return synth.p2p_walks(n_points=n or 10_000_000, shard=rank)
+        return synth.p2p_walks(n_points=n or 10_000_000, shard=rank, **g)
     if args.workload == "pip":
-        return synth.pip_stars(n_points=n or 1_000_000, shard=rank)
+        return synth.pip_stars(n_points=n or 1_000_000, shard=rank, **g)
     if args.workload == "pip3":
-        return synth.pip_tiles(n_points=n or 100_000_000, layer=args.layer, shard=rank)
+        return synth.pip_tiles(n_points=n or 100_000_000, layer=args.layer, shard=rank, **g)
     if args.workload == "p2p4":
-        return synth.p2p_walks_lognormal(n_points=n or 170_000_000, D=args.D, shard=rank)
+        return synth.p2p_walks_lognormal(n_points=n or 170_000_000, D=args.D, shard=rank, **g)
     raise ValueError(args.workload)
 
 
@@ -191,7 +194,7 @@ def metric_name(kind):
 
 def config_of(w, args):
     c = {"workload": w.name, "points": int(len(w.points)), "grid": f"{w.grid['nx']}x{w.grid['ny']}",
-         "form": args.form, "launch": "per_request", "pts_per_item": 64}
+         "form": args.form, "launch": "per_request", "pts_per_item": args.ppi or 64}
     big = len(w.points) * 16 > 129e6
     c["l2"] = ("inputs larger than L2 (points %d MB > 129 MB); no flush" % (len(w.points) * 16 // 10 ** 6) if big
                else "points %d MB fit in L2; steps re-read them (no flush)" % (len(w.points) * 16 // 10 ** 6))
@@ -235,7 +238,7 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=True):
+def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=True, ppi=0):
     import torch
     n = pts.shape[0]
     out_id = torch.empty(n, dtype=torch.int32, device=pts.device)
@@ -243,9 +246,10 @@ def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=Tru
 
     def one(time_refine):
         if w.kind == "p2p":
-            api.p2p_join(layer, pts, out_id, out_d, form=form, stream=stream, time_refine=time_refine)
+            api.p2p_join(layer, pts, out_id, out_d, form=form, stream=stream, time_refine=time_refine,
+                         pts_per_item=ppi)
         else:
-            api.pip_join(layer, pts, out_id, form=form, stream=stream, time_refine=time_refine)
+            api.pip_join(layer, pts, out_id, form=form, stream=stream, time_refine=time_refine, pts_per_item=ppi)
 
     for _ in range(warmup):
         one(False)
@@ -331,7 +335,7 @@ def run_ours(args):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
     gpu_index = int(vis) if vis.isdigit() else local
     with ClockSampler(gpu_index) as clk:
-        ms, st = time_joins(api, layer, w, pts, args.form, args.steps, args.warmup, world, stream)
+        ms, st = time_joins(api, layer, w, pts, args.form, args.steps, args.warmup, world, stream, ppi=args.ppi)
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world, dev)
     value = n * world * args.steps / (ms_max / 1000.0)
@@ -342,7 +346,7 @@ def run_ours(args):
              "edge_tests_per_s_algorithmic": st["algo_tests"] / (ms / 1000.0)}
     if not args.no_baselines and rank == 0 and args.form != "fp64":
         k64 = max(3, min(args.steps, 20))
-        ms64, st64 = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, stream)
+        ms64, st64 = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, stream, ppi=args.ppi)
         extra["fp64_plain"] = {"value": n * k64 / (ms64 / 1000.0), "unit": "points/s", "ms_per_step": ms64 / k64,
                                "roofline": roofline_of(w, "fp64", st64, props, measured_peaks())}
         extra["speedup_vs_fp64_plain"] = value / extra["fp64_plain"]["value"]
@@ -355,9 +359,11 @@ def run_ours(args):
         hd = torch.empty(n, dtype=torch.float64, pin_memory=True)
         ke = max(3, min(args.steps, 20))
         if w.kind == "p2p":
-            join_host = lambda: api.p2p_join_host(layer, hp, hid, hd, form=args.form, stream=stream)
+            join_host = lambda: api.p2p_join_host(layer, hp, hid, hd, form=args.form, stream=stream,
+                                                  pts_per_item=args.ppi)
         else:
-            join_host = lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream)
+            join_host = lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream,
+                                                  pts_per_item=args.ppi)
         for _ in range(2):
             join_host()
         torch.cuda.synchronize()

@@ -174,24 +174,26 @@ def p2p_join_noalloc(layer: Layer, pts, out_id: torch.Tensor, out_d: torch.Tenso
 
 
 def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, form: str = "fp64",
-                  stream=None) -> np.ndarray:
+                  stream=None, pts_per_item: int = 0) -> np.ndarray:
     """Same as pip_join from host memory (copies in and out; synchronous)."""
     p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
     n = p.shape[0]
     out = np.empty(n, np.int32) if out is None else out
-    o = _opts(form)
+    o = _opts(form, pts_per_item=pts_per_item)
     pp = p.data_ptr() if isinstance(p, torch.Tensor) else p.ctypes.data
     op = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
     L.check(L.lib().sj_pip_join_host(layer.handle, pp, n, op, C.byref(o), _stream(stream)), "sj_pip_join_host")
     return out
 
 
-def p2p_join_host(layer: Layer, pts, out_id=None, out_d=None, form: str = "fp64", stream=None):
+def p2p_join_host(layer: Layer, pts, out_id=None, out_d=None, form: str = "fp64", stream=None,
+                  pts_per_item: int = 0):
+    """Same as p2p_join from host memory (copies in and out; synchronous)."""
     p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
     n = p.shape[0]
     out_id = np.empty(n, np.int32) if out_id is None else out_id
     out_d = np.empty(n, np.float64) if out_d is None else out_d
-    o = _opts(form)
+    o = _opts(form, pts_per_item=pts_per_item)
     ptr = lambda a: a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
     L.check(L.lib().sj_p2p_join_host(layer.handle, ptr(p), n, ptr(out_id), ptr(out_d), C.byref(o), _stream(stream)),
             "sj_p2p_join_host")

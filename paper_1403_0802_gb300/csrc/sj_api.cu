@@ -26,6 +26,18 @@ cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, doubl
 cudaError_t launch_mbb(const LayerBuildArgs &a, cudaStream_t s);
 cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s);
+cudaError_t launch_segcell_count(const LayerBuildArgs &a, const float4 *seg32, const double2 *e64, int *seg_off,
+                                 unsigned long long *total, cudaStream_t s);
+cudaError_t launch_segcell_emit(const LayerBuildArgs &a, const float4 *seg32, const double2 *e64, const int *seg_off,
+                                int2 *pairs, int MS, const int *cand_ids, int *cseg_start, int *cseg_ids,
+                                int *cell_algo, cudaStream_t s);
+cudaError_t launch_prow_count(const LayerBuildArgs &a, int *prow_base, int *prow_r0, unsigned long long *total,
+                              cudaStream_t s);
+cudaError_t launch_prow_edge_count(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
+                                   int *cnt, unsigned long long *total, cudaStream_t s);
+cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
+                                  const int *cnt, int slots, int *prow_start, int *cursor, int *pedge_ids,
+                                  cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
@@ -135,6 +147,13 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.seg_e64 = L->seg_e64;
     ra.seg_inv64 = L->seg_inv64;
     ra.seg32 = L->seg32;
+    ra.cseg_start = L->cseg_start;
+    ra.cseg_ids = L->cseg_ids;
+    ra.cell_algo = L->cell_algo;
+    ra.prow_base = L->prow_base;
+    ra.prow_r0 = L->prow_r0;
+    ra.prow_start = L->prow_start;
+    ra.pedge_ids = L->pedge_ids;
     ra.D = L->D;
     ra.Df = L->Df;
     ra.Ddn = L->Ddn;
@@ -166,7 +185,8 @@ static void layer_free(sj_layer *L) {
     resolve_events(L);
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
-                    L->frames};
+                    L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->prow_base, L->prow_r0,
+                    L->prow_start, L->pedge_ids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -265,6 +285,131 @@ static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
     return SJ_OK;
 }
 
+// P2P per-cell segment lists (after build_candidates): every segment whose box
+// widened by D meets a cell is listed under that cell, sorted by segment index.
+static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
+    const int G = L->g.G, V = L->V;
+    CUDA_TRY(dalloc(&L->cseg_start, (size_t)G + 1));
+    CUDA_TRY(dalloc(&L->cell_algo, (size_t)G));
+    if (V == 0) {
+        L->MS = 0;
+        CUDA_TRY(dalloc(&L->cseg_ids, 0));
+        CUDA_TRY(cudaMemsetAsync(L->cseg_start, 0, sizeof(int) * ((size_t)G + 1), s));
+        CUDA_TRY(cudaMemsetAsync(L->cell_algo, 0, sizeof(int) * (size_t)G, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return SJ_OK;
+    }
+    LayerBuildArgs a{};
+    a.g = L->g;
+    a.kind = KIND_P2P;
+    a.D = L->D;
+    a.nobj = L->nobj;
+    a.V = V;
+    a.verts = L->verts;
+    a.obj_voff = L->obj_voff;
+    a.cand_start = L->cand_start;
+    struct Tmp {
+        void *p[7] = {};
+        ~Tmp() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } tmp;
+    int *seg_off = nullptr;
+    int2 *pairs = nullptr;
+    unsigned long long *total = nullptr;
+    const size_t nbs = (size_t)((std::max(G, V) + 4095) / 4096) + 2;
+    CUDA_TRY(dalloc(&a.cell_cnt, (size_t)G + 1)); tmp.p[0] = a.cell_cnt;
+    CUDA_TRY(dalloc(&a.cursor, (size_t)G)); tmp.p[1] = a.cursor;
+    CUDA_TRY(dalloc(&seg_off, (size_t)V + 1)); tmp.p[2] = seg_off;
+    CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[3] = a.block_sums;
+    CUDA_TRY(dalloc(&a.totals, 4)); tmp.p[4] = a.totals;
+    CUDA_TRY(dalloc(&total, 1)); tmp.p[5] = total;
+    CUDA_TRY(cudaMemsetAsync(a.cell_cnt, 0, sizeof(int) * ((size_t)G + 1), s));
+    CUDA_TRY(cudaMemsetAsync(a.cursor, 0, sizeof(int) * (size_t)G, s));
+    CUDA_TRY(cudaMemsetAsync(total, 0, sizeof(unsigned long long), s));
+    CUDA_TRY(launch_segcell_count(a, L->seg32, L->seg_e64, seg_off, total, s));
+    unsigned long long MS = 0;
+    CUDA_TRY(cudaMemcpyAsync(&MS, total, sizeof(MS), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (MS > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (cell, segment) pairs");
+    L->MS = (int64_t)MS;
+    CUDA_TRY(dalloc(&L->cseg_ids, (size_t)MS));
+    CUDA_TRY(dalloc(&pairs, (size_t)MS)); tmp.p[6] = pairs;
+    CUDA_TRY(launch_segcell_emit(a, L->seg32, L->seg_e64, seg_off, pairs, (int)MS, L->cand_ids, L->cseg_start,
+                                 L->cseg_ids, L->cell_algo, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SJ_OK;
+}
+
+// PIP per-(polygon, row) edge lists (after build_candidates).
+static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
+    const int P = L->nobj;
+    CUDA_TRY(dalloc(&L->prow_base, (size_t)P + 1));
+    CUDA_TRY(dalloc(&L->prow_r0, (size_t)P));
+    if (P == 0) {
+        L->MR = L->ME = 0;
+        CUDA_TRY(dalloc(&L->prow_start, 1));
+        CUDA_TRY(dalloc(&L->pedge_ids, 0));
+        CUDA_TRY(cudaMemsetAsync(L->prow_base, 0, sizeof(int), s));
+        CUDA_TRY(cudaMemsetAsync(L->prow_start, 0, sizeof(int), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return SJ_OK;
+    }
+    LayerBuildArgs a{};
+    a.g = L->g;
+    a.kind = KIND_PIP;
+    a.nobj = P;
+    a.V = L->V;
+    a.verts = L->verts;
+    a.obj_voff = L->obj_voff;
+    a.mbb = L->mbb;
+    struct Tmp {
+        void *p[5] = {};
+        ~Tmp() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } tmp;
+    unsigned long long *total = nullptr;
+    int *cnt = nullptr, *cursor = nullptr;
+    CUDA_TRY(dalloc(&total, 2)); tmp.p[0] = total;
+    CUDA_TRY(dalloc(&a.totals, 4)); tmp.p[1] = a.totals;
+    CUDA_TRY(cudaMemsetAsync(total, 0, 2 * sizeof(unsigned long long), s));
+    {
+        const size_t nbs = (size_t)((P + 4095) / 4096) + 2;
+        CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[2] = a.block_sums;
+    }
+    CUDA_TRY(launch_prow_count(a, L->prow_base, L->prow_r0, total, s));
+    unsigned long long MR = 0;
+    CUDA_TRY(cudaMemcpyAsync(&MR, total, sizeof(MR), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (MR > 2147483646ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 2 (polygon, row) slots");
+    L->MR = (int64_t)MR;
+    CUDA_TRY(dalloc(&cnt, (size_t)MR)); tmp.p[3] = cnt;
+    CUDA_TRY(dalloc(&cursor, (size_t)MR)); tmp.p[4] = cursor;
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)MR, s));
+    CUDA_TRY(cudaMemsetAsync(cursor, 0, sizeof(int) * (size_t)MR, s));
+    CUDA_TRY(launch_prow_edge_count(a, L->nxt, L->prow_base, L->prow_r0, cnt, total + 1, s));
+    unsigned long long ME = 0;
+    CUDA_TRY(cudaMemcpyAsync(&ME, total + 1, sizeof(ME), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (ME > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (polygon, row, edge) entries");
+    L->ME = (int64_t)ME;
+    CUDA_TRY(dalloc(&L->prow_start, (size_t)MR + 1));
+    CUDA_TRY(dalloc(&L->pedge_ids, (size_t)ME));
+    cudaFree(a.block_sums);
+    tmp.p[2] = nullptr;
+    {
+        const size_t nbs = (size_t)((MR + 4095) / 4096) + 2;
+        CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[2] = a.block_sums;
+    }
+    CUDA_TRY(launch_prow_edge_emit(a, L->nxt, L->prow_base, L->prow_r0, cnt, (int)MR, L->prow_start, cursor,
+                                   L->pedge_ids, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SJ_OK;
+}
+
 static sj_status layer_common_checks(const double *verts, int64_t V, const sj_grid *g, void *stream,
                                      sj_layer **out, DevInfo **di) {
     if (!out) return fail(SJ_ERR_INVALID, "out is NULL");
@@ -326,6 +471,8 @@ extern "C" sj_status sj_pip_layer_create(const double *verts, int64_t V, const i
     CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));
     st = build_candidates(L, dbad, s);
     if (st != SJ_OK) return st;
+    st = build_row_lists(L, s);
+    if (st != SJ_OK) return st;
     *out = L;
     guard.L = nullptr;
     return SJ_OK;
@@ -380,6 +527,8 @@ extern "C" sj_status sj_p2p_layer_create(const double *verts, int64_t V, const i
     CUDA_TRY(dalloc(&L->stats, ST_N));
     CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));
     st = build_candidates(L, dbad, s);
+    if (st != SJ_OK) return st;
+    st = build_seg_lists(L, s);
     if (st != SJ_OK) return st;
     *out = L;
     guard.L = nullptr;

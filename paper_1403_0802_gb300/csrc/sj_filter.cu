@@ -336,7 +336,9 @@ cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s
 
 // P2P segment table: for the segment that starts at vertex i of polyline l,
 // e = v[i+1] - v[i] and 1 / |e|^2 (0 for a zero-length segment, and for the
-// single vertex of a one-vertex polyline, which then acts as a point).
+// single vertex of a one-vertex polyline, which then acts as a point); the
+// fourth component holds l as int bits, or -1 for the last vertex of a
+// polyline of two or more vertices (which starts no segment).
 __global__ void k_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64,
                             float4 *seg32) {
     for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < L; l += gridDim.x * blockDim.x) {
@@ -351,7 +353,9 @@ __global__ void k_seg_table(const double2 *v, const int *line_off, int L, double
             }
             e64[i] = make_double2(ex, ey);
             inv64[i] = inv;
-            seg32[i] = make_float4(__double2float_rn(ex), __double2float_rn(ey), __double2float_rn(inv), 0.0f);
+            const int owner = (i + 1 < e || e - b == 1) ? l : -1;
+            seg32[i] = make_float4(__double2float_rn(ex), __double2float_rn(ey), __double2float_rn(inv),
+                                   __int_as_float(owner));
         }
     }
 }
@@ -429,10 +433,11 @@ __global__ void k_raster_emit(LayerBuildArgs a, int2 *pairs) {
     }
 }
 
-__global__ void k_cand_scatter(LayerBuildArgs a, const int2 *pairs, int M, int *cand_ids) {
+// (cell, id) pairs -> CSR lists (order within a cell fixed by k_cand_sort).
+__global__ void k_pair_scatter(const int2 *pairs, int M, const int *start, int *cursor, int *ids) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
         int2 p = pairs[k];
-        cand_ids[a.cand_start[p.x] + atomicAdd(&a.cursor[p.x], 1)] = p.y;
+        ids[start[p.x] + atomicAdd(&cursor[p.x], 1)] = p.y;
     }
 }
 
@@ -444,6 +449,134 @@ __global__ void k_cand_sort(const int *cand_start, int G, int *cand_ids) {
             int v = cand_ids[i], j = i - 1;
             while (j >= b && cand_ids[j] > v) { cand_ids[j + 1] = cand_ids[j]; --j; }
             cand_ids[j + 1] = v;
+        }
+    }
+}
+
+// ---- P2P per-cell segment lists.  A point p of cell c is within D of segment
+// [a, b] only if p lies in the segment's box widened by D; the cells of that
+// box (outward-rounded like the MBB filter above, and the same monotone FP64
+// cell rule as the points) therefore include c.  Listing, per cell, the
+// segments whose widened box meets it drops only segments farther than D from
+// every point of the cell, so the refinement may walk this list instead of all
+// segments of the cell's candidate polylines without changing any result.
+
+// Box of the segment starting at vertex i (b = a when e = b - a is zero, which
+// in IEEE arithmetic means b == a; a one-vertex polyline is its vertex).
+__device__ __forceinline__ Box seg_box(const double2 *v, const double2 *e64, int i) {
+    const double2 a = v[i], e = e64[i];
+    const double2 b = (e.x == 0.0 && e.y == 0.0) ? a : v[i + 1];
+    return Box{fmin(a.x, b.x), fmin(a.y, b.y), fmax(a.x, b.x), fmax(a.y, b.y)};
+}
+
+__device__ __forceinline__ long long seg_cell_count(const LayerBuildArgs &a, const float4 *seg32,
+                                                    const double2 *e64, int i, int4 &b) {
+    if (__float_as_int(seg32[i].w) < 0) return 0;
+    b = mbb_cell_box(a, seg_box(a.verts, e64, i));
+    return (long long)(b.z - b.x + 1) * (long long)(b.w - b.y + 1);
+}
+
+__global__ void k_segcell_count(LayerBuildArgs a, const float4 *seg32, const double2 *e64, int *seg_cells,
+                                unsigned long long *total) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < a.V; i0 += stride) {   // warp-uniform trip count
+        const int i = i0 + threadIdx.x;
+        unsigned long long n = 0;
+        if (i < a.V) {
+            int4 b;
+            const long long c = seg_cell_count(a, seg32, e64, i, b);
+            seg_cells[i] = c > 2147483647LL ? 2147483647 : (int)c;
+            n = (unsigned long long)c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
+        if (lane_id() == 0 && n) atomicAdd(total, n);
+    }
+}
+
+__global__ void k_segcell_emit(LayerBuildArgs a, const float4 *seg32, const double2 *e64, const int *seg_off,
+                               int *cell_cnt, int2 *pairs) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < a.V; i += gridDim.x * blockDim.x) {
+        int4 b;
+        if (seg_cell_count(a, seg32, e64, i, b) == 0) continue;
+        int k = seg_off[i];
+        for (int iy = b.y; iy <= b.w; ++iy)
+            for (int ix = b.x; ix <= b.z; ++ix) {
+                const int c = iy * a.g.nx + ix;
+                pairs[k++] = make_int2(c, i);
+                atomicAdd(&cell_cnt[c], 1);
+            }
+    }
+}
+
+// Per cell: the number of segments of its candidate polylines (the tests the
+// unfiltered refinement of Sec. III.B performs per point; statistics only).
+__global__ void k_cell_algo(const int *cand_start, const int *cand_ids, const int *obj_voff, int G, int *cell_algo) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
+        long long n = 0;
+        for (int k = cand_start[c]; k < cand_start[c + 1]; ++k) {
+            const int l = cand_ids[k], nv = obj_voff[l + 1] - obj_voff[l];
+            n += nv > 1 ? nv - 1 : 1;
+        }
+        cell_algo[c] = n > 2147483647LL ? 2147483647 : (int)n;
+    }
+}
+
+// ---- PIP per-(polygon, row) edge lists.  A point p of grid row r has p.y in
+// the row's band under the FP64 cell rule; an edge straddles p's horizontal
+// line only if min(ay, by) <= p.y < max(ay, by), and the row rule is monotone,
+// so r lies between the rows of the edge's two y values.  Listing, for each
+// candidate polygon and row, the edges whose row span includes the row drops
+// only edges that cannot cross the ray of any point in that row: the parity,
+// hence the result, is unchanged.
+
+// Rows of each polygon's MBB: prow_n[P] = r1 - r0 + 1 (scanned into the slot
+// bases afterwards), prow_r0[P] = r0, and the total in *total.
+__global__ void k_prow_count(LayerBuildArgs a, int *prow_n, int *prow_r0, unsigned long long *total) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < a.nobj; p0 += stride) {   // warp-uniform trip count
+        const int P = p0 + threadIdx.x;
+        unsigned long long n = 0;
+        if (P < a.nobj) {
+            const Box m = a.mbb[P];
+            const int r0 = clamped_axis(m.ymin, a.g.y0, a.g.ch, a.g.ny);
+            const int r1 = clamped_axis(m.ymax, a.g.y0, a.g.ch, a.g.ny);
+            prow_r0[P] = r0;
+            prow_n[P] = r1 - r0 + 1;
+            n = (unsigned long long)(r1 - r0 + 1);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
+        if (lane_id() == 0 && n) atomicAdd(total, n);
+    }
+}
+
+// One warp per polygon, lanes over its edges (vertex i -> nxt[i]).  Count pass
+// (ids == nullptr): cnt[slot] += 1 for every row of the edge, total in *total.
+// Emit pass: ids[start[slot] + cursor[slot]++] = i.
+__global__ void k_prow_edges(LayerBuildArgs a, const int *nxt, const int *prow_base, const int *prow_r0, int *cnt,
+                             unsigned long long *total, const int *start, int *cursor, int *ids) {
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int P = warp; P < a.nobj; P += nwarps) {
+        const int b = a.obj_voff[P], e = a.obj_voff[P + 1];
+        const int base = prow_base[P] - prow_r0[P];
+        unsigned long long n = 0;
+        for (int i = b + lane; i < e; i += 32) {
+            const double ya = a.verts[i].y, yb = a.verts[nxt[i]].y;
+            const int ra = clamped_axis(fmin(ya, yb), a.g.y0, a.g.ch, a.g.ny);
+            const int rb = clamped_axis(fmax(ya, yb), a.g.y0, a.g.ch, a.g.ny);
+            for (int r = ra; r <= rb; ++r) {
+                if (ids) ids[start[base + r] + atomicAdd(&cursor[base + r], 1)] = i;
+                else atomicAdd(&cnt[base + r], 1);
+            }
+            n += (unsigned long long)(rb - ra + 1);
+        }
+        if (!ids) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(FULL, n, o);
+            if (lane == 0) atomicAdd(total, n);
         }
     }
 }
@@ -489,8 +622,64 @@ cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int 
     k_raster_emit<<<stream_blocks(a.nobj, 128, 4096), 128, 0, s>>>(a, pairs);
     cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{a.cand_start}, a.g.G, a.block_sums, a.totals, s);
     if (e != cudaSuccess) return e;
-    k_cand_scatter<<<stream_blocks(M, 256, 4096), 256, 0, s>>>(a, pairs, M, cand_ids);
+    k_pair_scatter<<<stream_blocks(M, 256, 4096), 256, 0, s>>>(pairs, M, a.cand_start, a.cursor, cand_ids);
     k_cand_sort<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(a.cand_start, a.g.G, cand_ids);
+    return cudaGetLastError();
+}
+
+// Segment lists, step 1: cells per segment (into seg_off[V + 1]), their total,
+// and the exclusive offsets in place (V > 0; a.block_sums sized for V).
+cudaError_t launch_segcell_count(const LayerBuildArgs &a, const float4 *seg32, const double2 *e64, int *seg_off,
+                                 unsigned long long *total, cudaStream_t s) {
+    k_segcell_count<<<stream_blocks(a.V, 256, 4096), 256, 0, s>>>(a, seg32, e64, seg_off, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return run_scan(IntLoad{seg_off}, OffsetApply{seg_off}, a.V, a.block_sums, a.totals, s);
+}
+
+// Step 2: (cell, segment) pairs, per-cell counts (a.cell_cnt zeroed), CSR
+// offsets cseg_start, the lists (a.cursor zeroed) sorted by segment index, and
+// the per-cell candidate segment counts.
+cudaError_t launch_segcell_emit(const LayerBuildArgs &a, const float4 *seg32, const double2 *e64, const int *seg_off,
+                                int2 *pairs, int MS, const int *cand_ids, int *cseg_start, int *cseg_ids,
+                                int *cell_algo, cudaStream_t s) {
+    k_segcell_emit<<<stream_blocks(a.V, 128, 4096), 128, 0, s>>>(a, seg32, e64, seg_off, a.cell_cnt, pairs);
+    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{cseg_start}, a.g.G, a.block_sums, a.totals, s);
+    if (e != cudaSuccess) return e;
+    k_pair_scatter<<<stream_blocks(MS, 256, 4096), 256, 0, s>>>(pairs, MS, cseg_start, a.cursor, cseg_ids);
+    k_cand_sort<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(cseg_start, a.g.G, cseg_ids);
+    k_cell_algo<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(a.cand_start, cand_ids, a.obj_voff, a.g.G, cell_algo);
+    return cudaGetLastError();
+}
+
+// PIP row lists, step 1: rows per polygon and the slot bases (prow_base[P + 1],
+// exclusive scan in place); a.block_sums sized for max(G, P, slots).
+cudaError_t launch_prow_count(const LayerBuildArgs &a, int *prow_base, int *prow_r0, unsigned long long *total,
+                              cudaStream_t s) {
+    k_prow_count<<<stream_blocks(a.nobj, 256, 4096), 256, 0, s>>>(a, prow_base, prow_r0, total);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return run_scan(IntLoad{prow_base}, OffsetApply{prow_base}, a.nobj, a.block_sums, a.totals, s);
+}
+
+// Step 2 (count): edges per slot into cnt (zeroed), total entries in *total.
+cudaError_t launch_prow_edge_count(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
+                                   int *cnt, unsigned long long *total, cudaStream_t s) {
+    k_prow_edges<<<stream_blocks((long long)a.nobj * 32, 256, 4096), 256, 0, s>>>(a, nxt, prow_base, prow_r0, cnt,
+                                                                                 total, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+// Step 3 (emit): slot ranges prow_start[slots + 1] from cnt, then the lists
+// (cursor zeroed).  Order within a list is not fixed (parity is a XOR).
+cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
+                                  const int *cnt, int slots, int *prow_start, int *cursor, int *pedge_ids,
+                                  cudaStream_t s) {
+    cudaError_t e = run_scan(IntLoad{cnt}, OffsetApply{prow_start}, slots, a.block_sums, a.totals, s);
+    if (e != cudaSuccess) return e;
+    k_prow_edges<<<stream_blocks((long long)a.nobj * 32, 256, 4096), 256, 0, s>>>(a, nxt, prow_base, prow_r0, nullptr,
+                                                                                 nullptr, prow_start, cursor,
+                                                                                 pedge_ids);
     return cudaGetLastError();
 }
 

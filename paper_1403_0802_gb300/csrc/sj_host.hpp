@@ -34,10 +34,23 @@ struct sj_layer {
     int *poly_ring_off = nullptr;
     double2 *seg_e64 = nullptr;
     double *seg_inv64 = nullptr;
-    float4 *seg32 = nullptr;   // (fl32(ex), fl32(ey), fl32(1 / |e|^2), 0)
+    float4 *seg32 = nullptr;   // (fl32(ex), fl32(ey), fl32(1 / |e|^2), owner polyline id as bits or -1)
     sj::Box *mbb = nullptr;
     int *cand_start = nullptr;
     int *cand_ids = nullptr;
+    // P2P: per-cell segment lists (segments whose box widened by D meets the
+    // cell) and, per cell, the segment count of its candidate polylines.
+    int64_t MS = 0;
+    int *cseg_start = nullptr;
+    int *cseg_ids = nullptr;
+    int *cell_algo = nullptr;
+    // PIP: per-(polygon, grid row) edge lists (edges whose y-range rows include
+    // the row), polygon-major; see sj_filter.cu.
+    int64_t MR = 0, ME = 0;
+    int *prow_base = nullptr;    // [nobj + 1] first (polygon, row) slot of each polygon
+    int *prow_r0 = nullptr;      // [nobj] first row of each polygon's MBB
+    int *prow_start = nullptr;   // [MR + 1] list ranges in pedge_ids
+    int *pedge_ids = nullptr;    // [ME] edge (= first vertex) indices
     unsigned long long *stats = nullptr;
     unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins

@@ -172,7 +172,14 @@ struct RefineArgs {
     const float4 *vsplit;    // [V] (fl32(x), fl32(y), fl32(x - fl32(x)), fl32(y - fl32(y)))
     const double2 *seg_e64;  // P2P: [V] b - a of the segment starting at vertex i
     const double *seg_inv64; // P2P: [V] 1 / |b - a|^2 (0 for a degenerate segment)
-    const float4 *seg32;     // P2P: (fl32(ex), fl32(ey), fl32(1 / |e|^2), 0)
+    const float4 *seg32;     // P2P: (fl32(ex), fl32(ey), fl32(1 / |e|^2), owner polyline id bits)
+    const int *cseg_start;   // P2P: [G + 1] per-cell segment lists
+    const int *cseg_ids;     //      segment (= first vertex) indices, ascending per cell
+    const int *cell_algo;    //      [G] segments of the cell's candidate polylines
+    const int *prow_base;    // PIP: [P + 1] first (polygon, row) slot of each polygon
+    const int *prow_r0;      //      [P] first grid row of each polygon's MBB
+    const int *prow_start;   //      [slots + 1] edge list range of each (polygon, row)
+    const int *pedge_ids;    //      edge (= first vertex) indices
     double D;                // P2P window
     float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
     float Df;                // D rounded to FP32 (staging prune)

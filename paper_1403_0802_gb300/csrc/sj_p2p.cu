@@ -5,13 +5,15 @@
 // Work decomposition: one warp per (cell, point-chunk) item.
 //   1. The item's points are converted to cell-relative coordinates and their
 //      bounding box is reduced across the warp.
-//   2. Candidate polylines are taken 32 at a time (one per lane): their vertex
-//      ranges are read in parallel and their segment counts warp-scanned.
-//   3. Staging: the concatenated segments of the group are read 32 at a time;
-//      a segment whose bounding box is farther than D (plus a rounding slack)
-//      from the points' box cannot be within D of any point of the item and is
-//      dropped (exact: it cannot change any result); the others are compacted
-//      into shared memory (a, e = b - a, 1 / |e|^2, polyline id) with a ballot.
+//   2. The cell's segment list -- every segment of the candidate polylines
+//      whose box widened by D meets the cell, built with the layer; the others
+//      are farther than D from every point of the cell -- is read 32 segments
+//      at a time, one per lane.
+//   3. Staging: a segment whose bounding box is farther than D (plus a
+//      rounding slack) from the points' box cannot be within D of any point of
+//      the item and is dropped (exact: it cannot change any result); the others
+//      are compacted into shared memory (a, e = b - a, 1 / |e|^2, polyline id)
+//      with a ballot.
 //   4. Whenever the staging area fills, the warp splits its lanes into point
 //      groups of SG lanes (SG chosen so that np points x staged segments fill
 //      the warp); each lane strides over the staged segments keeping a running
@@ -59,7 +61,6 @@ struct P2PSmem<true> {
     static constexpr int SMAX = 128;
     float4 seg[SMAX];        // cell-relative a (x, y) and e (x, y)
     float2 si[SMAX];         // (1 / |e|^2, polyline id as bits)
-    int coff[33], cid[32], cvb[32];
     float2 pt[MAX_CH];
     float b1[MAX_CH], b2[MAX_CH];
     int i1[MAX_CH];
@@ -71,7 +72,6 @@ struct P2PSmem<false> {
     Seg64 seg[SMAX];
     double inv[SMAX];
     int sid[SMAX];
-    int coff[33], cid[32], cvb[32];
     double2 pt[MAX_CH];
     double b1[MAX_CH], b2[MAX_CH];
     int i1[MAX_CH];
@@ -241,84 +241,58 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         pmag = warp_max(pmag);
         float mag = pmag;   // FP32X: largest |cell-relative coordinate| refined for this item
         c_pairs += (unsigned long long)np * (unsigned long long)(k1 - k0);
+        c_algo += (unsigned long long)np * (unsigned long long)a.cell_algo[c];
 
-        for (int kg = k0; kg < k1; kg += 32) {
-            // 2. candidate group: one polyline per lane, segment counts scanned
-            const int nc = min(32, k1 - kg);
-            int lid = 0, vb = 0, nseg = 0;
-            if (lane < nc) {
-                lid = a.cand_ids[kg + lane];
-                vb = a.obj_voff[lid];
-                const int nv = a.obj_voff[lid + 1] - vb;
-                nseg = nv > 1 ? nv - 1 : 1;
+        // 2. the cell's segment list, 32 segments at a time (one per lane),
+        // 3. staging with the exact distance prune, 4. refinement when full
+        const int g0 = a.cseg_start[c], g1 = a.cseg_start[c + 1];
+        int nst = 0;
+        for (int base = g0; base < g1; base += 32) {
+            const int g = base + lane;
+            bool keep = false;
+            int i = 0, sid = 0;
+            float ax = 0.0f, ay = 0.0f, ex = 0.0f, ey = 0.0f, inv = 0.0f, smag = 0.0f;
+            if (g < g1) {
+                i = a.cseg_ids[g];
+                const float4 v = a.vsplit[i];
+                const float4 e = a.seg32[i];
+                sid = __float_as_int(e.w);
+                ax = rel_coord(v.x, v.z, fo.x);
+                ay = rel_coord(v.y, v.w, fo.y);
+                ex = e.x;
+                ey = e.y;
+                inv = e.z;
+                const float bx = ax + ex, by = ay + ey;
+                const float gx = fmaxf(0.0f, fmaxf(fminf(ax, bx) - bxhi, bxlo - fmaxf(ax, bx)));
+                const float gy = fmaxf(0.0f, fmaxf(fminf(ay, by) - byhi, bylo - fmaxf(ay, by)));
+                smag = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by)));
+                // rounding slack of the relative coordinates of both boxes (far above it)
+                const float lim = a.Df * (1.0f + 1e-6f) + 8.0f * U32 * (smag + pmag) + 8.0f * a.eps_abs;
+                keep = gx * gx + gy * gy <= lim * lim * (1.0f + 8.0f * U32);
             }
-            int incl = nseg;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int v = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += v;
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                const int pos = nst + __popc(bal & lt_mask);
+                if constexpr (FP32) {
+                    s.seg[pos] = make_float4(ax, ay, ex, ey);
+                    s.si[pos] = make_float2(inv, __int_as_float(sid));
+                    mag = fmaxf(mag, smag);
+                } else {
+                    const double2 v = a.verts[i], e = a.seg_e64[i];
+                    s.seg[pos] = Seg64{v.x, v.y, e.x, e.y};
+                    s.inv[pos] = a.seg_inv64[i];
+                    s.sid[pos] = sid;
+                }
             }
-            const int S = __shfl_sync(FULL, incl, 31);
-            __syncwarp();
-            if (lane < nc) {
-                s.coff[lane] = incl - nseg;
-                s.cid[lane] = lid;
-                s.cvb[lane] = vb;
-            }
-            if (lane == 0) s.coff[nc] = S;
-            __syncwarp();
-
-            // 3. staging with the exact distance prune, 4. refinement when full
-            c_algo += (unsigned long long)np * (unsigned long long)S;
-            int nst = 0, kw = 0;
-            for (int base = 0; base < S; base += 32) {
-                const int g = base + lane;
-                bool keep = false;
-                int i = 0, sid = 0;
-                float ax = 0.0f, ay = 0.0f, ex = 0.0f, ey = 0.0f, inv = 0.0f, smag = 0.0f;
-                if (g < S) {
-                    while (s.coff[kw + 1] <= g) ++kw;   // candidate of segment g (g grows by 32)
-                    i = s.cvb[kw] + (g - s.coff[kw]);
-                    sid = s.cid[kw];
-                    const float4 v = a.vsplit[i];
-                    const float4 e = a.seg32[i];
-                    ax = rel_coord(v.x, v.z, fo.x);
-                    ay = rel_coord(v.y, v.w, fo.y);
-                    ex = e.x;
-                    ey = e.y;
-                    inv = e.z;
-                    const float bx = ax + ex, by = ay + ey;
-                    const float gx = fmaxf(0.0f, fmaxf(fminf(ax, bx) - bxhi, bxlo - fmaxf(ax, bx)));
-                    const float gy = fmaxf(0.0f, fmaxf(fminf(ay, by) - byhi, bylo - fmaxf(ay, by)));
-                    smag = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by)));
-                    // rounding slack of the relative coordinates of both boxes (far above it)
-                    const float lim = a.Df * (1.0f + 1e-6f) + 8.0f * U32 * (smag + pmag) + 8.0f * a.eps_abs;
-                    keep = gx * gx + gy * gy <= lim * lim * (1.0f + 8.0f * U32);
+            nst += __popc(bal);
+            if (nst > SMAX - 32 || base + 32 >= g1) {
+                __syncwarp();
+                if (nst > 0) {
+                    p2p_compute<FP32>(s, np, nst, lane);
+                    c_tests += (unsigned long long)np * (unsigned long long)nst;
                 }
-                const unsigned bal = __ballot_sync(FULL, keep);
-                if (keep) {
-                    const int pos = nst + __popc(bal & lt_mask);
-                    if constexpr (FP32) {
-                        s.seg[pos] = make_float4(ax, ay, ex, ey);
-                        s.si[pos] = make_float2(inv, __int_as_float(sid));
-                        mag = fmaxf(mag, smag);
-                    } else {
-                        const double2 v = a.verts[i], e = a.seg_e64[i];
-                        s.seg[pos] = Seg64{v.x, v.y, e.x, e.y};
-                        s.inv[pos] = a.seg_inv64[i];
-                        s.sid[pos] = sid;
-                    }
-                }
-                nst += __popc(bal);
-                if (nst > SMAX - 32 || base + 32 >= S) {
-                    __syncwarp();
-                    if (nst > 0) {
-                        p2p_compute<FP32>(s, np, nst, lane);
-                        c_tests += (unsigned long long)np * (unsigned long long)nst;
-                    }
-                    __syncwarp();
-                    nst = 0;
-                }
+                __syncwarp();
+                nst = 0;
             }
         }
         if constexpr (FP32) mag = warp_max(mag);
@@ -379,7 +353,8 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
 }
 
 // FP64 recomputation of the points the FP32X pass could not certify: one warp
-// per point, lanes over each candidate's segments, warp min per polyline.
+// per point, lanes over the cell's segment list, each lane keeping the
+// smallest (squared distance, polyline id), then a warp fold.
 __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
     const int lane = lane_id();
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -391,31 +366,22 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
         const int2 e = a.fb[f];
         const int j = e.x, c = e.y;
         const double2 p = a.spts[j];
-        double best = INF;
-        int bid = -1;
-        for (int k = a.cand_start[c]; k < a.cand_start[c + 1]; ++k) {
-            const int lid = a.cand_ids[k];
-            const int vb = a.obj_voff[lid], nv = a.obj_voff[lid + 1] - vb;
-            const int nseg = nv > 1 ? nv - 1 : 1;
-            double m = INF;
-            for (int t = lane; t < nseg; t += 32) {
-                const int i = vb + t;
-                const double2 v = a.verts[i], ev = a.seg_e64[i];
-                m = fmin(m, seg_d2(p.x, p.y, v.x, v.y, ev.x, ev.y, a.seg_inv64[i]));
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(FULL, m, o));
-            const double d = sqrt(m);
-            if (d < best) { best = d; bid = lid; }
+        Best<double> st{INF, INF, -1};
+        for (int g = a.cseg_start[c] + lane; g < a.cseg_start[c + 1]; g += 32) {
+            const int i = a.cseg_ids[g];
+            const double2 v = a.verts[i], ev = a.seg_e64[i];
+            consider<false>(st, seg_d2(p.x, p.y, v.x, v.y, ev.x, ev.y, a.seg_inv64[i]), __float_as_int(a.seg32[i].w));
         }
-        const bool hit = bid >= 0 && best <= a.D;
+        for (int o = 16; o > 0; o >>= 1) st = merge<false>(st, shfl_best<false>(st, o));
+        const double best = sqrt(st.b1);
+        const bool hit = st.i1 >= 0 && best <= a.D;
         if (lane == 0) {
             if (a.res_id) {
-                a.res_id[j] = hit ? bid : -1;
+                a.res_id[j] = hit ? st.i1 : -1;
                 if (a.res_d) a.res_d[j] = hit ? best : INF;
             } else if (hit) {
                 const int i = a.perm[j];
-                a.out_id[i] = bid;
+                a.out_id[i] = st.i1;
                 if (a.out_d) a.out_d[i] = best;
             }
             if (hit) ++c_hits;

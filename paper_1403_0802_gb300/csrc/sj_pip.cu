@@ -7,7 +7,9 @@
 //   1. The item's points are loaded; the range [ymin, ymax] of their FP32
 //      y roundings is reduced across the warp.
 //   2. Candidate polygons are taken 32 at a time (one per lane, in id order):
-//      vertex ranges read in parallel, edge counts warp-scanned.
+//      each lane reads its polygon's edge list for the item's grid row (the
+//      edges whose y-range spans that row, built with the layer; no other edge
+//      can cross the ray of a point in the row), list lengths warp-scanned.
 //   3. Staging: the concatenated edges of the group are read 32 at a time; an
 //      edge whose y-range lies strictly below ymin or strictly above ymax
 //      cannot straddle the horizontal line of any point of the item and is
@@ -192,6 +194,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
         const int j0 = a.cell_start[c] + item.y;
         const int np = min(a.ch, a.cell_start[c + 1] - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
+        const int row = c / a.g.nx;
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
         // 1. points and the range of their FP32 y truncations
@@ -224,15 +227,19 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             for (int q = lane; q < np; q += 32) pending += (s.found[q] < 0);
             pending = __reduce_add_sync(FULL, pending);
             if (pending == 0) break;
-            // 2. candidate group: one polygon per lane, edge counts scanned
+            // 2. candidate group: one polygon per lane, its edge list for the
+            //    item's grid row, list lengths scanned
             const int nc = min(32, k1 - kg);
-            int pid = 0, vb = 0, ne = 0;
+            int pid = 0, vb = 0, ne = 0, nall = 0;
             if (lane < nc) {
                 pid = a.cand_ids[kg + lane];
-                vb = a.obj_voff[pid];
-                ne = a.obj_voff[pid + 1] - vb;
+                const int slot = a.prow_base[pid] + (row - a.prow_r0[pid]);
+                vb = a.prow_start[slot];
+                ne = a.prow_start[slot + 1] - vb;
+                nall = a.obj_voff[pid + 1] - a.obj_voff[pid];
             }
             c_pairs += (unsigned long long)pending * (unsigned long long)nc;
+            c_algo += (unsigned long long)pending * (unsigned long long)__reduce_add_sync(FULL, (unsigned)nall);
             int incl = ne;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -250,7 +257,6 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             __syncwarp();
 
             // 3. staging with the exact y-range prune, 4. parity when full
-            c_algo += (unsigned long long)pending * (unsigned long long)E;
             int nst = 0, kw = 0;
             for (int base = 0; base < E; base += 32) {
                 const int g = base + lane;
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
                 if (g < E) {
                     while (s.coff[kw + 1] <= g) ++kw;   // candidate of edge g (g grows by 32)
                     k = kw;
-                    i = s.cvb[kw] + (g - s.coff[kw]);
+                    i = a.pedge_ids[s.cvb[kw] + (g - s.coff[kw])];
                     j = a.nxt[i];
                     va = a.vsplit[i];
                     vc = a.vsplit[j];

@@ -261,6 +261,13 @@ class Workload:
     meta: dict = field(default_factory=dict)
 
 
+def _count(n: int) -> str:
+    """10_000_000 -> "10M", 100_000 -> "100k", 1_500 -> "1500" (workload names)."""
+    if n >= 1_000_000 and n % 1_000_000 == 0:
+        return f"{n // 1_000_000}M"
+    return f"{n // 1000}k" if n >= 1000 and n % 1000 == 0 else str(n)
+
+
 def _point_rng(rng: np.random.Generator, seed: int, shard: int) -> np.random.Generator:
     """Points of shard 0 continue the layer's generator; shard k > 0 (another
     rank of a weak-scaling run) draws its own points from (seed, k), so every
@@ -275,19 +282,21 @@ def pip_stars(n_points: int = 1_000_000, seed: int = SEED_BASE + 1, n_side: int 
     rng = np.random.default_rng(seed)
     layer = star_polygons(rng, n_side=n_side)
     pts = points_uniform(n_points, _point_rng(rng, seed, shard))
-    return Workload("pip_1M_stars1024_grid256", "pip", pts, grid(grid_n), polygons=layer)
+    return Workload(f"pip_{_count(n_points)}_stars{n_side * n_side}_grid{grid_n}", "pip", pts, grid(grid_n),
+                    polygons=layer)
 
 
 def p2p_walks(n_points: int = 10_000_000, n_lines: int = 100_000, seed: int = SEED_BASE + 2,
-              D: float = 100.0, grid_n: int = 1024, shard: int = 0) -> Workload:
+              D: float = 100.0, grid_n: int = 512, shard: int = 0) -> Workload:
     """P2P, plain FP64 method: mixture points against random-walk polylines with
-    2-40 vertices, window D = 100 m, filter grid 1024 x 1024."""
+    2-40 vertices, window D = 100 m, filter grid 512 x 512 (the fastest of
+    256..2048 per axis on GB300 with per-cell segment lists)."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(2, 41, size=n_lines)
     layer = random_walks(rng, sizes)
     pts = points_mixture(n_points, _point_rng(rng, seed, shard))
-    return Workload("p2p_10M_walks100k_D100_grid1024", "p2p", pts, grid(grid_n),
-                    polylines=layer, D=float(D))
+    return Workload(f"p2p_{_count(n_points)}_walks{_count(n_lines)}_D{int(D)}_grid{grid_n}", "p2p", pts,
+                    grid(grid_n), polylines=layer, D=float(D))
 
 
 def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE + 3,
@@ -302,7 +311,7 @@ def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE
     else:
         P = tiling(rng, 140, 100, side_median=90.0, side_cap=25000, n_giant=3)
     pts = points_mixture(n_points, _point_rng(np.random.default_rng(seed), seed, shard))
-    return Workload(f"pip_{n_points}_tiles{P.n_polygons}_grid{grid_n}", "pip", pts, grid(grid_n), polygons=P)
+    return Workload(f"pip_{_count(n_points)}_tiles{P.n_polygons}_L{layer}_grid{grid_n}", "pip", pts, grid(grid_n), polygons=P)
 
 
 def p2p_walks_lognormal(n_points: int = 170_000_000, n_lines: int = 150_000,
@@ -314,5 +323,5 @@ def p2p_walks_lognormal(n_points: int = 170_000_000, n_lines: int = 150_000,
     sizes = np.clip(np.round(rng.lognormal(math.log(8.0), 0.8, size=n_lines)), 2, 200).astype(np.int64)
     layer = random_walks(rng, sizes)
     pts = points_mixture(n_points, _point_rng(rng, seed, shard))
-    return Workload(f"p2p_{n_points}_walks{n_lines}_D{int(D)}_grid{grid_n}", "p2p", pts,
+    return Workload(f"p2p_{_count(n_points)}_walks{_count(n_lines)}_D{int(D)}_grid{grid_n}", "p2p", pts,
                     grid(grid_n), polylines=layer, D=float(D))
