@@ -377,7 +377,8 @@ def run_ours(args):
                "timing": "host wall clock around synchronous calls (pinned buffers)"}
 
     cpu = cpu_baseline(w) if (rank == 0 and world == 1 and not args.no_baselines) else None
-    kernels_per_join = 5 + 1 + (1 if (w.kind == "p2p" and args.form == "fp32x") else 0)
+    # cell_hist, 3 scan phases, scatter; refine; FP32X P2P recheck; unsort
+    kernels_per_join = 5 + 1 + (1 if (w.kind == "p2p" and args.form == "fp32x") else 0) + 1
     if rank == 0:
         line = {
             "metric": metric_name(w.kind), "value": value, "unit": "points/s", "n_gpus": world,

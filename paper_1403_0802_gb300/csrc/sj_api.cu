@@ -229,7 +229,7 @@ static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
     int *cell_cnt = nullptr, *cursor = nullptr, *obj_cells = nullptr, *totals = nullptr;
     int2 *block_sums = nullptr, *pairs = nullptr;
     unsigned long long *total = nullptr;
-    size_t nbs = (size_t)((std::max(L->g.G, L->nobj) + 4095) / 4096) + 2;
+    size_t nbs = bucket_scan_blocks(std::max(L->g.G, L->nobj));
     struct Tmp {
         void *p[7] = {};
         ~Tmp() {
@@ -250,6 +250,7 @@ static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
     a.cursor = cursor;
     a.obj_cells = obj_cells;
     a.block_sums = block_sums;
+    a.bs_cap = nbs;
     a.totals = totals;
 
     if (L->nobj > 0) {
@@ -318,11 +319,12 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     int *seg_off = nullptr;
     int2 *pairs = nullptr;
     unsigned long long *total = nullptr;
-    const size_t nbs = (size_t)((std::max(G, V) + 4095) / 4096) + 2;
+    const size_t nbs = bucket_scan_blocks(std::max(G, V));
     CUDA_TRY(dalloc(&a.cell_cnt, (size_t)G + 1)); tmp.p[0] = a.cell_cnt;
     CUDA_TRY(dalloc(&a.cursor, (size_t)G)); tmp.p[1] = a.cursor;
     CUDA_TRY(dalloc(&seg_off, (size_t)V + 1)); tmp.p[2] = seg_off;
     CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[3] = a.block_sums;
+    a.bs_cap = nbs;
     CUDA_TRY(dalloc(&a.totals, 4)); tmp.p[4] = a.totals;
     CUDA_TRY(dalloc(&total, 1)); tmp.p[5] = total;
     CUDA_TRY(cudaMemsetAsync(a.cell_cnt, 0, sizeof(int) * ((size_t)G + 1), s));
@@ -377,8 +379,9 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     CUDA_TRY(dalloc(&a.totals, 4)); tmp.p[1] = a.totals;
     CUDA_TRY(cudaMemsetAsync(total, 0, 2 * sizeof(unsigned long long), s));
     {
-        const size_t nbs = (size_t)((P + 4095) / 4096) + 2;
+        const size_t nbs = bucket_scan_blocks(P);
         CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[2] = a.block_sums;
+        a.bs_cap = nbs;
     }
     CUDA_TRY(launch_prow_count(a, L->prow_base, L->prow_r0, total, s));
     unsigned long long MR = 0;
@@ -401,8 +404,9 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     cudaFree(a.block_sums);
     tmp.p[2] = nullptr;
     {
-        const size_t nbs = (size_t)((MR + 4095) / 4096) + 2;
+        const size_t nbs = bucket_scan_blocks((int)MR);
         CUDA_TRY(dalloc(&a.block_sums, nbs)); tmp.p[2] = a.block_sums;
+        a.bs_cap = nbs;
     }
     CUDA_TRY(launch_prow_edge_emit(a, L->nxt, L->prow_base, L->prow_r0, cnt, (int)MR, L->prow_start, cursor,
                                    L->pedge_ids, s));
@@ -595,22 +599,31 @@ extern "C" sj_status sj_layer_reset_stats(sj_layer *L) {
 // ------------------------------------------------------------------ joins
 
 struct JoinBufs {
-    int *cnt, *cell_start, *perm, *totals;
+    int *cnt, *cell_start, *perm, *totals, *pos, *res_id, *cell_base;
     int2 *key_rank, *items, *block_sums, *fb;
     double2 *spts;
+    double *res_d;
 };
 
-static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb) {
+// with_spts: also a cell-ordered copy of the points (else the refinement reads
+// the input points through perm).  sorted_res: cell-ordered results res_id
+// (and res_d when with_d) plus each input point's slot pos, for launch_unsort.
+static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb, bool with_spts = true,
+                  bool sorted_res = false, bool with_d = false) {
     size_t max_items = (size_t)(N / ch) + (size_t)std::min<int64_t>(G, N) + 1;
     b.cnt = s.take<int>((size_t)G + 1);
     b.cell_start = s.take<int>((size_t)G + 1);
     b.totals = s.take<int>(4);
     b.key_rank = s.take<int2>((size_t)N);
     b.perm = s.take<int>((size_t)N);
-    b.spts = s.take<double2>((size_t)N);
+    b.spts = with_spts ? s.take<double2>((size_t)N) : nullptr;
     b.items = s.take<int2>(max_items);
     b.block_sums = s.take<int2>(bucket_scan_blocks(G));
     b.fb = need_fb ? s.take<int2>((size_t)N) : nullptr;
+    b.pos = sorted_res ? s.take<int>((size_t)N) : nullptr;
+    b.cell_base = sorted_res ? s.take<int>((size_t)G) : nullptr;
+    b.res_id = sorted_res ? s.take<int>((size_t)N) : nullptr;
+    b.res_d = (sorted_res && with_d) ? s.take<double>((size_t)N) : nullptr;
 }
 
 static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
@@ -642,10 +655,11 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     const bool need_fb = (kind == KIND_P2P && form == SJ_FP32X);
 
     JoinBufs b;
-    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb); });
+    const bool with_d = kind == KIND_P2P && out_d != nullptr;
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, true, with_d); });
     Scratch sc;
     CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
-    carve(sc, b, N, G, ch, need_fb);
+    carve(sc, b, N, G, ch, need_fb, false, true, with_d);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * ((size_t)G + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
 
@@ -662,9 +676,10 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ba.ch = ch;
     ba.items = b.items;
     ba.block_sums = b.block_sums;
+    ba.bs_cap = bucket_scan_blocks(G);
     ba.totals = b.totals;
-    ba.out_id = out_id;
-    ba.out_d = kind == KIND_P2P ? out_d : nullptr;
+    ba.pos = b.pos;
+    ba.cell_base = b.cell_base;
     if (e == cudaSuccess) e = launch_bucket(ba, s);
 
     RefineArgs ra{};
@@ -674,9 +689,10 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ra.cell_start = b.cell_start;
     ra.perm = b.perm;
     ra.spts = b.spts;
+    ra.pts = (const double2 *)pts;
     ra.ch = ch;
-    ra.out_id = out_id;
-    ra.out_d = out_d;
+    ra.res_id = b.res_id;   // cell-ordered results, every slot of a refined cell written
+    ra.res_d = b.res_d;
     ra.fb = b.fb;
     ra.n_fb = b.totals + 2;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -699,6 +715,8 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
         std::lock_guard<std::mutex> lk(L->ev_mu);
         L->ev_pending.emplace_back(ev0, ev1);
     }
+    // a8: results to input order
+    if (e == cudaSuccess) e = launch_unsort(b.pos, b.res_id, b.res_d, (int)N, out_id, with_d ? out_d : nullptr, s);
     cudaError_t e2 = cudaFreeAsync(sc.base, s);
     if (e != cudaSuccess) return cuda_fail(e, "join launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
@@ -787,6 +805,7 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
     ba.cell_start = cell_start;
     ba.perm = perm;
     ba.block_sums = bs;
+    ba.bs_cap = bucket_scan_blocks(gd.G);
     ba.totals = totals;
     ba.ch = 1;
     cudaError_t e = cudaMemsetAsync(cnt, 0, sizeof(int) * ((size_t)gd.G + 1), s);
@@ -898,6 +917,7 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     ba.ch = NOALLOC_CH;
     ba.items = b.items;
     ba.block_sums = b.block_sums;
+    ba.bs_cap = bucket_scan_blocks(G);
     ba.totals = b.totals;
     ba.out_id = out_id;
     ba.out_d = out_d;

@@ -203,6 +203,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     ba.ch = E->ch;
     ba.items = items;
     ba.block_sums = block_sums;
+    ba.bs_cap = bucket_scan_blocks(G);
     ba.totals = totals;
 
     RefineArgs &ra = w->ra;

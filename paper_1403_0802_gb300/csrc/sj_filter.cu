@@ -14,7 +14,7 @@ namespace sj {
 // ------------------------------------------------------------------ block scan helpers
 
 constexpr int SCAN_T = 256;
-constexpr int SCAN_V = 16;
+constexpr int SCAN_V = 4;     // 1,024 elements per tile: >= 256 tiles for a 512 x 512 grid
 constexpr int SCAN_TILE = SCAN_T * SCAN_V;
 
 __device__ __forceinline__ int2 add2(int2 a, int2 b) { return make_int2(a.x + b.x, a.y + b.y); }
@@ -56,6 +56,7 @@ template <class Load>
 __global__ void __launch_bounds__(SCAN_T) k_scan_reduce(Load ld, int n, int2 *block_sums) {
     int base = blockIdx.x * SCAN_TILE;
     int2 s = make_int2(0, 0);
+#pragma unroll
     for (int k = threadIdx.x; k < SCAN_TILE; k += SCAN_T) {
         int c = base + k;
         if (c < n) s = add2(s, ld(c));
@@ -106,10 +107,13 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(Load ld, Apply ap, int n,
     }
 }
 
+// block_sums must hold at least nb + 1 entries (bucket_scan_blocks(n) does);
+// a smaller capacity is an error, not an out-of-bounds write.
 template <class Load, class Apply>
-static cudaError_t run_scan(Load ld, Apply ap, int n, int2 *block_sums, int *totals, cudaStream_t s) {
+static cudaError_t run_scan(Load ld, Apply ap, int n, int2 *block_sums, size_t cap, int *totals, cudaStream_t s) {
     int nb = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (nb == 0) nb = 1;
+    if ((size_t)nb + 1 > cap) return cudaErrorInvalidValue;
     k_scan_reduce<Load><<<nb, SCAN_T, 0, s>>>(ld, n, block_sums);
     k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, totals);
     k_scan_apply<Load, Apply><<<nb, SCAN_T, 0, s>>>(ld, ap, n, block_sums);
@@ -214,8 +218,10 @@ struct BucketApply {
     int *cell_start;
     int2 *items;
     int ch;
+    int *cell_base;   // optional: cell_start of cells that yield items, else -1
     __device__ void operator()(int c, int2 ex, int2 v, int n) const {
         cell_start[c] = ex.x;
+        if (cell_base) cell_base[c] = v.y > 0 ? ex.x : -1;
         if (c == n - 1) cell_start[n] = ex.x + v.x;
         if (items)
             for (int t = 0; t < v.y; ++t) items[ex.y + t] = make_int2(c, t * ch);
@@ -236,14 +242,56 @@ __global__ void k_scatter(BucketArgs a) {
                 if (a.spts) p[u] = a.pts[i];
             }
         }
+        // With a.pos (cell_base set): only points of cells that yield work
+        // items get a slot; the others, like points outside the grid, get -1.
+        const int *base = a.pos ? a.cell_base : a.cell_start;
         int pos[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) pos[u] = k[u].x < a.g.G ? a.cell_start[k[u].x] + k[u].y : -1;
+        for (int u = 0; u < UNR; ++u) {
+            pos[u] = -1;
+            if (k[u].x < a.g.G) {
+                const int b = base[k[u].x];
+                pos[u] = b >= 0 ? b + k[u].y : -1;
+            }
+        }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             if (pos[u] >= 0) {
                 a.perm[pos[u]] = i0 + u * T;
                 if (a.spts) a.spts[pos[u]] = p[u];
+            }
+        }
+        if (a.pos) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const int i = i0 + u * T;
+                if (i < a.n) a.pos[i] = pos[u];
+            }
+        }
+    }
+}
+
+// a8 for cell-ordered results (see launch_unsort).
+__global__ void k_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id,
+                         double *out_d) {
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const int T = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+        int j[UNR], id[UNR];
+        double d[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < n) ? pos[i0 + u * T] : -1;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            id[u] = j[u] >= 0 ? res_id[j[u]] : -1;
+            if (out_d) d[u] = j[u] >= 0 ? res_d[j[u]] : inf;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            if (i < n) {
+                out_id[i] = id[u];
+                if (out_d) out_d[i] = d[u];
             }
         }
     }
@@ -259,15 +307,22 @@ static int stream_blocks(long long n, int per_block, int cap) {
 // The scan alone (per-cell counts already in a.cnt): cell_start, work items
 // and totals.  Grid size depends only on G, so the launch can be replayed.
 cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
-    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch}, a.g.G,
-                    a.block_sums, a.totals, s);
+    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch, a.cell_base}, a.g.G,
+                    a.block_sums, a.bs_cap, a.totals, s);
+}
+
+cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id, double *out_d,
+                          cudaStream_t s) {
+    const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
+    k_unsort<<<nb, 256, 0, s>>>(pos, res_id, res_d, n, out_id, out_d);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s) {
     int nb = stream_blocks(a.n, 256, 152 * 32);
     k_cell_hist<<<nb, 256, 0, s>>>(a);
-    cudaError_t e = run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch},
-                             a.g.G, a.block_sums, a.totals, s);
+    cudaError_t e = run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch, a.cell_base},
+                             a.g.G, a.block_sums, a.bs_cap, a.totals, s);
     if (e != cudaSuccess) return e;
     k_scatter<<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();
@@ -441,14 +496,31 @@ __global__ void k_pair_scatter(const int2 *pairs, int M, const int *start, int *
     }
 }
 
-// Sort each cell's candidate ids ascending (insertion sort; lists are short).
+// Sort each cell's ids ascending: Shell sort with Ciura's gap sequence
+// (1, 4, 10, 23, 57, 132, 301, 701, then x 2.25), one thread per cell.  Lists
+// are short in the common case (one or two gap passes), and a long
+// one (a large D makes every object a candidate of every cell) stays near
+// n^1.3 instead of the n^2 of plain insertion.
 __global__ void k_cand_sort(const int *cand_start, int G, int *cand_ids) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
-        int b = cand_start[c], e = cand_start[c + 1];
-        for (int i = b + 1; i < e; ++i) {
-            int v = cand_ids[i], j = i - 1;
-            while (j >= b && cand_ids[j] > v) { cand_ids[j + 1] = cand_ids[j]; --j; }
-            cand_ids[j + 1] = v;
+        const int b = cand_start[c], n = cand_start[c + 1] - b;
+        int *v = cand_ids + b;
+        const int ciura[8] = {1, 4, 10, 23, 57, 132, 301, 701};
+        int gaps[32];
+        int ng = 0;
+        while (ng < 8 && ciura[ng] < n) { gaps[ng] = ciura[ng]; ++ng; }
+        if (ng == 8) {
+            long long g = 701;
+            while (ng < 32 && (g = g * 9 / 4) < n) gaps[ng++] = (int)g;
+        }
+        for (int t = ng - 1; t >= 0; --t) {
+            const int h = gaps[t];
+            for (int i = h; i < n; ++i) {
+                const int x = v[i];
+                int j = i;
+                while (j >= h && v[j - h] > x) { v[j] = v[j - h]; j -= h; }
+                v[j] = x;
+            }
         }
     }
 }
@@ -616,11 +688,11 @@ cudaError_t launch_raster_count(const LayerBuildArgs &a, unsigned long long *tot
     if (e != cudaSuccess) return e;
     // Counts -> exclusive offsets in place: every tile loads its counts into
     // registers before it writes, and tiles write only their own indices.
-    return run_scan(IntLoad{a.obj_cells}, OffsetApply{a.obj_cells}, a.nobj, a.block_sums, a.totals, s);
+    return run_scan(IntLoad{a.obj_cells}, OffsetApply{a.obj_cells}, a.nobj, a.block_sums, a.bs_cap, a.totals, s);
 }
 cudaError_t launch_raster_emit(const LayerBuildArgs &a, int2 *pairs, int M, int *cand_ids, cudaStream_t s) {
     k_raster_emit<<<stream_blocks(a.nobj, 128, 4096), 128, 0, s>>>(a, pairs);
-    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{a.cand_start}, a.g.G, a.block_sums, a.totals, s);
+    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{a.cand_start}, a.g.G, a.block_sums, a.bs_cap, a.totals, s);
     if (e != cudaSuccess) return e;
     k_pair_scatter<<<stream_blocks(M, 256, 4096), 256, 0, s>>>(pairs, M, a.cand_start, a.cursor, cand_ids);
     k_cand_sort<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(a.cand_start, a.g.G, cand_ids);
@@ -634,7 +706,7 @@ cudaError_t launch_segcell_count(const LayerBuildArgs &a, const float4 *seg32, c
     k_segcell_count<<<stream_blocks(a.V, 256, 4096), 256, 0, s>>>(a, seg32, e64, seg_off, total);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return run_scan(IntLoad{seg_off}, OffsetApply{seg_off}, a.V, a.block_sums, a.totals, s);
+    return run_scan(IntLoad{seg_off}, OffsetApply{seg_off}, a.V, a.block_sums, a.bs_cap, a.totals, s);
 }
 
 // Step 2: (cell, segment) pairs, per-cell counts (a.cell_cnt zeroed), CSR
@@ -644,7 +716,7 @@ cudaError_t launch_segcell_emit(const LayerBuildArgs &a, const float4 *seg32, co
                                 int2 *pairs, int MS, const int *cand_ids, int *cseg_start, int *cseg_ids,
                                 int *cell_algo, cudaStream_t s) {
     k_segcell_emit<<<stream_blocks(a.V, 128, 4096), 128, 0, s>>>(a, seg32, e64, seg_off, a.cell_cnt, pairs);
-    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{cseg_start}, a.g.G, a.block_sums, a.totals, s);
+    cudaError_t e = run_scan(IntLoad{a.cell_cnt}, OffsetApply{cseg_start}, a.g.G, a.block_sums, a.bs_cap, a.totals, s);
     if (e != cudaSuccess) return e;
     k_pair_scatter<<<stream_blocks(MS, 256, 4096), 256, 0, s>>>(pairs, MS, cseg_start, a.cursor, cseg_ids);
     k_cand_sort<<<stream_blocks(a.g.G, 128, 8192), 128, 0, s>>>(cseg_start, a.g.G, cseg_ids);
@@ -659,7 +731,7 @@ cudaError_t launch_prow_count(const LayerBuildArgs &a, int *prow_base, int *prow
     k_prow_count<<<stream_blocks(a.nobj, 256, 4096), 256, 0, s>>>(a, prow_base, prow_r0, total);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return run_scan(IntLoad{prow_base}, OffsetApply{prow_base}, a.nobj, a.block_sums, a.totals, s);
+    return run_scan(IntLoad{prow_base}, OffsetApply{prow_base}, a.nobj, a.block_sums, a.bs_cap, a.totals, s);
 }
 
 // Step 2 (count): edges per slot into cnt (zeroed), total entries in *total.
@@ -675,7 +747,7 @@ cudaError_t launch_prow_edge_count(const LayerBuildArgs &a, const int *nxt, cons
 cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
                                   const int *cnt, int slots, int *prow_start, int *cursor, int *pedge_ids,
                                   cudaStream_t s) {
-    cudaError_t e = run_scan(IntLoad{cnt}, OffsetApply{prow_start}, slots, a.block_sums, a.totals, s);
+    cudaError_t e = run_scan(IntLoad{cnt}, OffsetApply{prow_start}, slots, a.block_sums, a.bs_cap, a.totals, s);
     if (e != cudaSuccess) return e;
     k_prow_edges<<<stream_blocks((long long)a.nobj * 32, 256, 4096), 256, 0, s>>>(a, nxt, prow_base, prow_r0, nullptr,
                                                                                  nullptr, prow_start, cursor,

@@ -163,7 +163,8 @@ struct RefineArgs {
     const int *n_items;      // device count
     const int *cell_start;   // [G + 1] sorted point ranges
     const int *perm;         // sorted slot -> input index
-    const double2 *spts;     // sorted points (FP64)
+    const double2 *spts;     // sorted points (FP64), or null: the point of slot j is pts[perm[j]]
+    const double2 *pts;      // input points (used when spts is null)
     const int *cand_start;   // [G + 1]
     const int *cand_ids;     // [M]
     const int *obj_voff;     // [nobj + 1] first vertex of each polygon / polyline
@@ -196,6 +197,11 @@ struct RefineArgs {
     unsigned long long *stats;
 };
 
+// FP64 point of sorted slot j.
+__device__ __forceinline__ double2 slot_point(const RefineArgs &a, int j) {
+    return a.spts ? a.spts[j] : a.pts[a.perm[j]];
+}
+
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);
 cudaError_t launch_p2p_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);
@@ -209,17 +215,25 @@ struct BucketArgs {
     int2 *key_rank;      // [n] (cell, rank within cell)
     int *cell_start;     // [G + 1]
     int *perm;           // [n]
-    double2 *spts;       // [n] or null
+    double2 *spts;       // [n] cell-ordered copy of the points, or null (not written)
     const int *cand_start;  // layer candidates (null: no work items)
     int ch;
     int2 *items;         // work items or null
     int2 *block_sums;    // scan scratch
+    size_t bs_cap;       // its capacity in int2 (launches fail when it is too small)
     int *totals;         // [2]: in-grid points, items
     int *out_id;         // initialised to -1 (or null)
     double *out_d;       // initialised to +inf (or null)
+    int *pos;            // [n] sorted slot of each input point, -1 when its cell has no
+                         //     candidates or it lies outside the grid (or null)
+    int *cell_base;      // [G] with pos: cell_start of cells that yield work items, else -1
 };
 size_t bucket_scan_blocks(int G);
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s);
+// a8 for cell-ordered results: out[i] = res[pos[i]], or -1 / +inf where
+// pos[i] < 0 (one pass; out_d and res_d may be null).
+cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id, double *out_d,
+                          cudaStream_t s);
 
 struct LayerBuildArgs {
     GridDev g;
@@ -234,6 +248,7 @@ struct LayerBuildArgs {
     int *cursor;             // [G] zeroed
     int *obj_cells;          // [nobj + 1]
     int2 *block_sums;
+    size_t bs_cap;           // capacity of block_sums in int2
     int *totals;
     int *bad;                // validation flags
 };

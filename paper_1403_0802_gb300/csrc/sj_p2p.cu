@@ -106,9 +106,11 @@ struct Best {
 template <bool FP32, typename T>
 __device__ __forceinline__ void consider(Best<T> &s, T d, int l) {
     if constexpr (FP32) {
-        const bool lt = d < s.b1, same = (l == s.i1);
-        const T nb2 = lt ? (same ? s.b2 : s.b1) : ((!same && d < s.b2) ? d : s.b2);
-        s.b1 = lt ? d : s.b1;
+        // b1 <= b2 always; the runner-up becomes max(d, b1) when l is another
+        // polyline (whichever of the old best and d is not the new best).
+        const bool lt = d < s.b1;
+        const T nb2 = (l == s.i1) ? s.b2 : fminf(s.b2, fmaxf(d, s.b1));
+        s.b1 = fminf(s.b1, d);
         s.i1 = lt ? l : s.i1;
         s.b2 = nb2;
     } else {
@@ -222,7 +224,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         // 1. points: cell-relative FP32 coordinates, their box and magnitude
         float bxlo = FINF, bxhi = -FINF, bylo = FINF, byhi = -FINF, pmag = 0.0f;
         for (int q = lane; q < np; q += 32) {
-            const double2 p = a.spts[j0 + q];
+            const double2 p = slot_point(a, j0 + q);
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
     for (int f = warp; f < n; f += nwarps) {
         const int2 e = a.fb[f];
         const int j = e.x, c = e.y;
-        const double2 p = a.spts[j];
+        const double2 p = slot_point(a, j);
         Best<double> st{INF, INF, -1};
         for (int g = a.cseg_start[c] + lane; g < a.cseg_start[c + 1]; g += 32) {
             const int i = a.cseg_ids[g];

@@ -58,6 +58,7 @@ struct PipSmem<true> {
     int coff[33], cid[32], cvb[32];
     float2 pt[MAX_CH];
     float pyh[MAX_CH];
+    int pin[MAX_CH];          // FP64 source index of the point: sorted slot (spts) or input index (pts)
     int found[MAX_CH];
     unsigned par[MAX_CH];
 };
@@ -85,10 +86,11 @@ __device__ __forceinline__ int cross64(double px, double py, double ax, double a
     return d > 0.0;
 }
 
-// FP64 re-evaluation of edge i (vertex i -> nxt[i]) for sorted point j.
-__device__ __noinline__ int cross64_global(const RefineArgs &a, int i, int j) {
-    double2 p = a.spts[j];
-    double2 A = a.verts[i], B = a.verts[a.nxt[i]];
+// FP64 re-evaluation of edge i (vertex i -> nxt[i]) for point k of spts (when
+// set) or of pts.
+__device__ __noinline__ int cross64_global(const RefineArgs &a, int i, int k) {
+    const double2 p = a.spts ? a.spts[k] : a.pts[k];
+    const double2 A = a.verts[i], B = a.verts[a.nxt[i]];
     return cross64(p.x, p.y, A.x, A.y, B.x, B.y);
 }
 
@@ -142,7 +144,7 @@ __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, cons
                 for (int t = sub; t < ns; t += sg) {
                     const float2 yh = s.yh[t];
                     if ((yh.x == pyh) | (yh.y == pyh)) {   // FP32 y tie: decide in FP64
-                        m ^= (unsigned)cross64_global(a, s.vi[t], j0 + q) << s.kk[t];
+                        m ^= (unsigned)cross64_global(a, s.vi[t], s.pin[q]) << s.kk[t];
                         ++c_fb;
                         continue;
                     }
@@ -156,7 +158,7 @@ __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, cons
                     if (orient32(p.x, p.y, lx, ly, hx, hy, a.eps_abs, pos)) {
                         cr = (int)pos;
                     } else {
-                        cr = cross64_global(a, s.vi[t], j0 + q);
+                        cr = cross64_global(a, s.vi[t], s.pin[q]);
                         ++c_fb;
                     }
                     m ^= (unsigned)cr << s.kk[t];
@@ -200,13 +202,14 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
         // 1. points and the range of their FP32 y truncations
         float ylo = FINF, yhi = -FINF;
         for (int q = lane; q < np; q += 32) {
-            const double2 p = a.spts[j0 + q];
+            const double2 p = slot_point(a, j0 + q);
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
             if constexpr (FP32) {
                 s.pt[q] = make_float2(rel_coord(hx, lx, fo.x), rel_coord(hy, ly, fo.y));
                 s.pyh[q] = hy;
+                s.pin[q] = a.spts ? j0 + q : a.perm[j0 + q];
             } else {
                 s.pt[q] = p;
             }
