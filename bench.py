@@ -27,6 +27,7 @@ the timed region is bracketed by barriers and the slowest rank's time is used.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -291,6 +292,35 @@ def build_layer(api, w, dev, stream):
     return layer, t0.elapsed_time(t1)
 
 
+HERE = os.path.dirname(os.path.abspath(__file__))
+REFINE_SOURCES = {"p2p": ("paper_1403_0802_gb300/csrc/sj_p2p.cu", "paper_1403_0802_gb300/csrc/sj_internal.cuh"),
+                  "pip": ("paper_1403_0802_gb300/csrc/sj_pip.cu", "paper_1403_0802_gb300/csrc/sj_internal.cuh")}
+
+
+def sources_sha(kind):
+    h = hashlib.sha256()
+    for f in REFINE_SOURCES[kind]:
+        with open(os.path.join(HERE, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel, workload, kind):
+    """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
+    committed ncu summary profiles/traffic.txt (lines: kernel workload bytes
+    sha256-of-the-kernel's-sources), or None when absent or when the sources
+    changed since the counters were taken."""
+    path = os.path.join(HERE, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = sources_sha(kind)
+    for line in open(path):
+        f = line.split()
+        if len(f) == 4 and not line.startswith("#") and f[0] == kernel and f[1] == workload and f[3] == sha:
+            return float(f[2])
+    return None
+
+
 def roofline_of(w, form, st, props, peaks):
     """Dominant kernel = the refinement launch, timed with CUDA events on the
     join's stream.  Work per launch = the (point, edge or segment) tests the
@@ -306,8 +336,10 @@ def roofline_of(w, form, st, props, peaks):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak = props.multi_processor_count * lanes * 2 * sm_mhz * 1e6 / 1e12
     achieved = executed * fpt / (refine_ms / 1e3) / 1e12 if refine_ms > 0 else None
-    return {"bound": "alu", "kernel": f"k_{w.kind}_refine<{form}>", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak if achieved else None, "traffic": None,
+    kernel = f"k_{w.kind}_refine<{form}>"
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
+            "traffic": measured_traffic(kernel, w.name, w.kind),
             "peak_source": f"derived: {props.multi_processor_count} SMs x {lanes} "
                            f"{'FP32' if form == 'fp32x' else 'FP64'} lanes x 2 flops x {sm_mhz:.0f} MHz "
                            f"(MEASURED_PEAKS sm_max_mhz)",

@@ -602,14 +602,19 @@ struct JoinBufs {
     int *cnt, *cell_start, *perm, *totals, *pos, *res_id, *cell_base;
     int2 *key_rank, *items, *block_sums, *fb;
     double2 *spts;
-    double *res_d;
+    ResF *resf;
+    ResD *resd;
 };
 
+// Result layout of a join: through perm into the outputs (RES_PERM), or
+// cell-ordered and gathered back through pos: ids only (RES_IDS, PIP) or packed
+// P2P records (RES_F for FP32X, RES_D for FP64).
+enum { RES_PERM = 0, RES_IDS, RES_F, RES_D };
+
 // with_spts: also a cell-ordered copy of the points (else the refinement reads
-// the input points through perm).  sorted_res: cell-ordered results res_id
-// (and res_d when with_d) plus each input point's slot pos, for launch_unsort.
+// the input points through perm).
 static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb, bool with_spts = true,
-                  bool sorted_res = false, bool with_d = false) {
+                  int res = RES_PERM) {
     size_t max_items = (size_t)(N / ch) + (size_t)std::min<int64_t>(G, N) + 1;
     b.cnt = s.take<int>((size_t)G + 1);
     b.cell_start = s.take<int>((size_t)G + 1);
@@ -620,10 +625,12 @@ static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_f
     b.items = s.take<int2>(max_items);
     b.block_sums = s.take<int2>(bucket_scan_blocks(G));
     b.fb = need_fb ? s.take<int2>((size_t)N) : nullptr;
+    const bool sorted_res = res != RES_PERM;
     b.pos = sorted_res ? s.take<int>((size_t)N) : nullptr;
     b.cell_base = sorted_res ? s.take<int>((size_t)G) : nullptr;
-    b.res_id = sorted_res ? s.take<int>((size_t)N) : nullptr;
-    b.res_d = (sorted_res && with_d) ? s.take<double>((size_t)N) : nullptr;
+    b.res_id = res == RES_IDS ? s.take<int>((size_t)N) : nullptr;
+    b.resf = res == RES_F ? s.take<ResF>((size_t)N) : nullptr;
+    b.resd = res == RES_D ? s.take<ResD>((size_t)N) : nullptr;
 }
 
 static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
@@ -655,11 +662,11 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     const bool need_fb = (kind == KIND_P2P && form == SJ_FP32X);
 
     JoinBufs b;
-    const bool with_d = kind == KIND_P2P && out_d != nullptr;
-    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, true, with_d); });
+    const int res = kind == KIND_PIP ? RES_IDS : (form == SJ_FP32X ? RES_F : RES_D);
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res); });
     Scratch sc;
     CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
-    carve(sc, b, N, G, ch, need_fb, false, true, with_d);
+    carve(sc, b, N, G, ch, need_fb, false, res);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * ((size_t)G + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
 
@@ -692,7 +699,10 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ra.pts = (const double2 *)pts;
     ra.ch = ch;
     ra.res_id = b.res_id;   // cell-ordered results, every slot of a refined cell written
-    ra.res_d = b.res_d;
+    ra.resf = b.resf;
+    ra.resd = b.resd;
+    ra.out_id = out_id;     // FP32X recheck: final outputs through perm
+    ra.out_d = out_d;
     ra.fb = b.fb;
     ra.n_fb = b.totals + 2;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -703,20 +713,22 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
         if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
     }
     if (e == cudaSuccess) {
-        if (kind == KIND_PIP) {
-            e = launch_pip_refine(ra, form, 4, di->sms * di->pip_bps[form], s);
-        } else {
-            e = launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s);
-            if (e == cudaSuccess && need_fb) e = launch_p2p_recheck(ra, di->sms * 4, s);
-        }
+        if (kind == KIND_PIP) e = launch_pip_refine(ra, form, 4, di->sms * di->pip_bps[form], s);
+        else e = launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s);
     }
-    if (timed && ev1) {
+    if (timed && ev1) {   // the refinement launch alone
         if (e == cudaSuccess) e = cudaEventRecord(ev1, s);
         std::lock_guard<std::mutex> lk(L->ev_mu);
         L->ev_pending.emplace_back(ev0, ev1);
     }
-    // a8: results to input order
-    if (e == cudaSuccess) e = launch_unsort(b.pos, b.res_id, b.res_d, (int)N, out_id, with_d ? out_d : nullptr, s);
+    // a8: results to input order; then the FP32X recheck overwrites the points
+    // it redoes in FP64, through perm
+    if (e == cudaSuccess) {
+        if (res == RES_IDS) e = launch_unsort(b.pos, b.res_id, nullptr, (int)N, out_id, nullptr, s);
+        else if (res == RES_F) e = launch_unsort_f(b.pos, b.resf, (int)N, out_id, out_d, s);
+        else e = launch_unsort_d(b.pos, b.resd, (int)N, out_id, out_d, s);
+    }
+    if (e == cudaSuccess && need_fb) e = launch_p2p_recheck(ra, di->sms * 4, s);
     cudaError_t e2 = cudaFreeAsync(sc.base, s);
     if (e != cudaSuccess) return cuda_fail(e, "join launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");

@@ -311,6 +311,42 @@ cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
                     a.block_sums, a.bs_cap, a.totals, s);
 }
 
+// Packed records: one gather per point.  FP32X distances widen exactly.
+template <typename R>
+__global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, double *out_d) {
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const int T = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+        int j[UNR];
+        R r[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < n) ? pos[i0 + u * T] : -1;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (j[u] >= 0) r[u] = res[j[u]];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int i = i0 + u * T;
+            if (i < n) {
+                out_id[i] = j[u] >= 0 ? r[u].id : -1;
+                if (out_d) out_d[i] = j[u] >= 0 ? (double)r[u].d : inf;
+            }
+        }
+    }
+}
+
+cudaError_t launch_unsort_f(const int *pos, const ResF *res, int n, int *out_id, double *out_d, cudaStream_t s) {
+    const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
+    k_unsort_rec<ResF><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unsort_d(const int *pos, const ResD *res, int n, int *out_id, double *out_d, cudaStream_t s) {
+    const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
+    k_unsort_rec<ResD><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id, double *out_d,
                           cudaStream_t s) {
     const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);

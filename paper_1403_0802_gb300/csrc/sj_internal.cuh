@@ -156,6 +156,18 @@ enum { KIND_PIP = 0, KIND_P2P = 1 };
 // Per-layer device counters (index into sj_run_stats order after `joins`).
 enum { ST_POINTS = 0, ST_ITEMS, ST_PAIRS, ST_TESTS, ST_FALLBACK, ST_HITS, ST_ALGO, ST_N };
 
+// Cell-ordered P2P results of a per-request join, one record per slot so that
+// the final gather to input order reads one place per point.
+struct ResF {            // FP32X: id and the certified FP32 distance (+inf on a miss)
+    int id;
+    float d;
+};
+struct alignas(16) ResD {  // FP64
+    int id;
+    int pad;
+    double d;
+};
+
 // Arguments of the refinement kernels.
 struct RefineArgs {
     GridDev g;
@@ -192,6 +204,9 @@ struct RefineArgs {
     double *out_d;
     int *res_id;             // when set: results in sorted order for every slot
     double *res_d;           //   (hits and misses); out_id / perm unused
+    ResF *resf;              // P2P FP32X: packed sorted results (instead of res_id / res_d);
+                             //   the FP64 recheck then writes out_id / out_d through perm
+    ResD *resd;              // P2P FP64: packed sorted results
     int2 *fb;                // P2P FP32X: points to redo in FP64 (sorted slot, cell)
     int *n_fb;
     unsigned long long *stats;
@@ -234,6 +249,8 @@ cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s);
 // pos[i] < 0 (one pass; out_d and res_d may be null).
 cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id, double *out_d,
                           cudaStream_t s);
+cudaError_t launch_unsort_f(const int *pos, const ResF *res, int n, int *out_id, double *out_d, cudaStream_t s);
+cudaError_t launch_unsort_d(const int *pos, const ResD *res, int n, int *out_id, double *out_d, cudaStream_t s);
 
 struct LayerBuildArgs {
     GridDev g;

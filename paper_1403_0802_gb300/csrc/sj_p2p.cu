@@ -302,6 +302,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             const int id = s.i1[q];
             int out = -1;
             double dd = __longlong_as_double(0x7ff0000000000000LL);
+            float df = FINF;
             if (id >= 0) {
                 if constexpr (FP32) {
                     const float d = sqrtf(s.b1[q]), d2 = sqrtf(s.b2[q]);
@@ -319,6 +320,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                         }
                         out = id;
                         dd = widen(d);
+                        df = d;
                     }
                 } else {
                     const double d = sqrt(s.b1[q]);
@@ -328,7 +330,11 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                     }
                 }
             }
-            if (a.res_id) {
+            if (a.resf) {
+                a.resf[j0 + q] = ResF{out, df};
+            } else if (a.resd) {
+                a.resd[j0 + q] = ResD{out, 0, dd};
+            } else if (a.res_id) {
                 a.res_id[j0 + q] = out;
                 if (a.res_d) a.res_d[j0 + q] = dd;
             } else if (out >= 0) {
@@ -381,10 +387,10 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
             if (a.res_id) {
                 a.res_id[j] = hit ? st.i1 : -1;
                 if (a.res_d) a.res_d[j] = hit ? best : INF;
-            } else if (hit) {
+            } else {   // final outputs through perm (hits and misses)
                 const int i = a.perm[j];
-                a.out_id[i] = st.i1;
-                if (a.out_d) a.out_d[i] = best;
+                a.out_id[i] = hit ? st.i1 : -1;
+                if (a.out_d) a.out_d[i] = hit ? best : INF;
             }
             if (hit) ++c_hits;
         }
