@@ -38,6 +38,9 @@ cudaError_t launch_prow_edge_count(const LayerBuildArgs &a, const int *nxt, cons
 cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const int *prow_base, const int *prow_r0,
                                   const int *cnt, int slots, int *prow_start, int *cursor, int *pedge_ids,
                                   cudaStream_t s);
+cudaError_t launch_cseg_records(const int *cseg_start, const int *cseg_ids, const GridDev &g, const float *frame_x,
+                                const float *frame_y, const float4 *vsplit, const float4 *seg32, float4 *rec,
+                                cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
@@ -150,6 +153,7 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.cseg_start = L->cseg_start;
     ra.cseg_ids = L->cseg_ids;
     ra.cell_algo = L->cell_algo;
+    ra.cseg_rec = L->cseg_rec;
     ra.prow_base = L->prow_base;
     ra.prow_r0 = L->prow_r0;
     ra.prow_start = L->prow_start;
@@ -185,7 +189,7 @@ static void layer_free(sj_layer *L) {
     resolve_events(L);
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
-                    L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->prow_base, L->prow_r0,
+                    L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
                     L->prow_start, L->pedge_ids};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -295,6 +299,7 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     if (V == 0) {
         L->MS = 0;
         CUDA_TRY(dalloc(&L->cseg_ids, 0));
+        CUDA_TRY(dalloc(&L->cseg_rec, 0));
         CUDA_TRY(cudaMemsetAsync(L->cseg_start, 0, sizeof(int) * ((size_t)G + 1), s));
         CUDA_TRY(cudaMemsetAsync(L->cell_algo, 0, sizeof(int) * (size_t)G, s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -340,6 +345,9 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     CUDA_TRY(dalloc(&pairs, (size_t)MS)); tmp.p[6] = pairs;
     CUDA_TRY(launch_segcell_emit(a, L->seg32, L->seg_e64, seg_off, pairs, (int)MS, L->cand_ids, L->cseg_start,
                                  L->cseg_ids, L->cell_algo, s));
+    CUDA_TRY(dalloc(&L->cseg_rec, 2 * (size_t)MS));
+    CUDA_TRY(launch_cseg_records(L->cseg_start, L->cseg_ids, L->g, L->frames, L->frames + L->g.nx, L->vsplit,
+                                 L->seg32, L->cseg_rec, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
 }

@@ -617,6 +617,28 @@ __global__ void k_segcell_emit(LayerBuildArgs a, const float4 *seg32, const doub
     }
 }
 
+// FP32X staging records of the segment lists, two float4 per entry g of cell c:
+//   rec[2g]     = (ax, ay, ex, ey): a relative to the cell's FP32 frame origin
+//                 (rel_coord of the (hi, lo) split, the refinement's own rule)
+//                 and fl32(b - a);
+//   rec[2g + 1] = (fl32(1 / |e|^2), owner polyline id bits,
+//                  max(|ax|, |ay|, |ax + ex|, |ay + ey|), segment index bits).
+__global__ void k_cseg_records(const int *cseg_start, const int *cseg_ids, int G, int nx, const float *frame_x,
+                               const float *frame_y, const float4 *vsplit, const float4 *seg32, float4 *rec) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
+        const float2 fo = cell_frame(frame_x, frame_y, nx, c);
+        for (int g = cseg_start[c]; g < cseg_start[c + 1]; ++g) {
+            const int i = cseg_ids[g];
+            const float4 v = vsplit[i], e = seg32[i];
+            const float ax = rel_coord(v.x, v.z, fo.x), ay = rel_coord(v.y, v.w, fo.y);
+            const float bx = ax + e.x, by = ay + e.y;
+            const float mag = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by)));
+            rec[2 * (size_t)g] = make_float4(ax, ay, e.x, e.y);
+            rec[2 * (size_t)g + 1] = make_float4(e.z, e.w, mag, __int_as_float(i));
+        }
+    }
+}
+
 // Per cell: the number of segments of its candidate polylines (the tests the
 // unfiltered refinement of Sec. III.B performs per point; statistics only).
 __global__ void k_cell_algo(const int *cand_start, const int *cand_ids, const int *obj_voff, int G, int *cell_algo) {
@@ -788,6 +810,14 @@ cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const
     k_prow_edges<<<stream_blocks((long long)a.nobj * 32, 256, 4096), 256, 0, s>>>(a, nxt, prow_base, prow_r0, nullptr,
                                                                                  nullptr, prow_start, cursor,
                                                                                  pedge_ids);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cseg_records(const int *cseg_start, const int *cseg_ids, const GridDev &g, const float *frame_x,
+                                const float *frame_y, const float4 *vsplit, const float4 *seg32, float4 *rec,
+                                cudaStream_t s) {
+    k_cseg_records<<<stream_blocks(g.G, 128, 8192), 128, 0, s>>>(cseg_start, cseg_ids, g.G, g.nx, frame_x, frame_y,
+                                                                vsplit, seg32, rec);
     return cudaGetLastError();
 }
 

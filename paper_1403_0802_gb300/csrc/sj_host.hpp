@@ -44,6 +44,8 @@ struct sj_layer {
     int *cseg_start = nullptr;
     int *cseg_ids = nullptr;
     int *cell_algo = nullptr;
+    float4 *cseg_rec = nullptr;   // [2 MS] per list entry: cell-relative (ax, ay, ex, ey) and
+                                  // (1 / |e|^2, owner id bits, magnitude bound, segment index bits)
     // PIP: per-(polygon, grid row) edge lists (edges whose y-range rows include
     // the row), polygon-major; see sj_filter.cu.
     int64_t MR = 0, ME = 0;

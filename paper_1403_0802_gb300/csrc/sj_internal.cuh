@@ -189,6 +189,7 @@ struct RefineArgs {
     const int *cseg_start;   // P2P: [G + 1] per-cell segment lists
     const int *cseg_ids;     //      segment (= first vertex) indices, ascending per cell
     const int *cell_algo;    //      [G] segments of the cell's candidate polylines
+    const float4 *cseg_rec;  //      [2 MS] FP32X staging records of the list entries (see sj_filter.cu)
     const int *prow_base;    // PIP: [P + 1] first (polygon, row) slot of each polygon
     const int *prow_r0;      //      [P] first grid row of each polygon's MBB
     const int *prow_start;   //      [slots + 1] edge list range of each (polygon, row)

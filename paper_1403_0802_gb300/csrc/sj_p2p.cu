@@ -7,8 +7,9 @@
 //      bounding box is reduced across the warp.
 //   2. The cell's segment list -- every segment of the candidate polylines
 //      whose box widened by D meets the cell, built with the layer; the others
-//      are farther than D from every point of the cell -- is read 32 segments
-//      at a time, one per lane.
+//      are farther than D from every point of the cell -- is read 32 entries
+//      at a time, one per lane, as records prepared with the layer (the
+//      segment relative to this cell's FP32 frame, its owner and magnitude).
 //   3. Staging: a segment whose bounding box is farther than D (plus a
 //      rounding slack) from the points' box cannot be within D of any point of
 //      the item and is dropped (exact: it cannot change any result); the others
@@ -255,19 +256,18 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             int i = 0, sid = 0;
             float ax = 0.0f, ay = 0.0f, ex = 0.0f, ey = 0.0f, inv = 0.0f, smag = 0.0f;
             if (g < g1) {
-                i = a.cseg_ids[g];
-                const float4 v = a.vsplit[i];
-                const float4 e = a.seg32[i];
-                sid = __float_as_int(e.w);
-                ax = rel_coord(v.x, v.z, fo.x);
-                ay = rel_coord(v.y, v.w, fo.y);
-                ex = e.x;
-                ey = e.y;
-                inv = e.z;
+                const float4 r0 = a.cseg_rec[2 * (size_t)g], r1 = a.cseg_rec[2 * (size_t)g + 1];
+                ax = r0.x;
+                ay = r0.y;
+                ex = r0.z;
+                ey = r0.w;
+                inv = r1.x;
+                sid = __float_as_int(r1.y);
+                smag = r1.z;
+                i = __float_as_int(r1.w);
                 const float bx = ax + ex, by = ay + ey;
                 const float gx = fmaxf(0.0f, fmaxf(fminf(ax, bx) - bxhi, bxlo - fmaxf(ax, bx)));
                 const float gy = fmaxf(0.0f, fmaxf(fminf(ay, by) - byhi, bylo - fmaxf(ay, by)));
-                smag = fmaxf(fmaxf(fabsf(ax), fabsf(ay)), fmaxf(fabsf(bx), fabsf(by)));
                 // rounding slack of the relative coordinates of both boxes (far above it)
                 const float lim = a.Df * (1.0f + 1e-6f) + 8.0f * U32 * (smag + pmag) + 8.0f * a.eps_abs;
                 keep = gx * gx + gy * gy <= lim * lim * (1.0f + 8.0f * U32);
