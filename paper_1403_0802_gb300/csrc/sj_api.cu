@@ -41,6 +41,8 @@ cudaError_t launch_prow_edge_emit(const LayerBuildArgs &a, const int *nxt, const
 cudaError_t launch_cseg_records(const int *cseg_start, const int *cseg_ids, const GridDev &g, const float *frame_x,
                                 const float *frame_y, const float4 *vsplit, const float4 *seg32, float4 *rec,
                                 cudaStream_t s);
+cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *nxt, const float4 *vsplit,
+                                float4 *rec, cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
@@ -158,6 +160,7 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.prow_r0 = L->prow_r0;
     ra.prow_start = L->prow_start;
     ra.pedge_ids = L->pedge_ids;
+    ra.pedge_rec = L->pedge_rec;
     ra.D = L->D;
     ra.Df = L->Df;
     ra.Ddn = L->Ddn;
@@ -190,7 +193,7 @@ static void layer_free(sj_layer *L) {
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
                     L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
-                    L->prow_start, L->pedge_ids};
+                    L->prow_start, L->pedge_ids, L->pedge_rec};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -361,6 +364,7 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
         L->MR = L->ME = 0;
         CUDA_TRY(dalloc(&L->prow_start, 1));
         CUDA_TRY(dalloc(&L->pedge_ids, 0));
+        CUDA_TRY(dalloc(&L->pedge_rec, 0));
         CUDA_TRY(cudaMemsetAsync(L->prow_base, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(L->prow_start, 0, sizeof(int), s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -418,6 +422,8 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     }
     CUDA_TRY(launch_prow_edge_emit(a, L->nxt, L->prow_base, L->prow_r0, cnt, (int)MR, L->prow_start, cursor,
                                    L->pedge_ids, s));
+    CUDA_TRY(dalloc(&L->pedge_rec, 2 * (size_t)ME));
+    if (ME > 0) CUDA_TRY(launch_prow_records(L->pedge_ids, (long long)ME, L->nxt, L->vsplit, L->pedge_rec, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
 }

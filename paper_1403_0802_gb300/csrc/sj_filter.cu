@@ -821,4 +821,21 @@ cudaError_t launch_cseg_records(const int *cseg_start, const int *cseg_ids, cons
     return cudaGetLastError();
 }
 
+// FP32X staging records of the PIP row lists: the (hi, lo) splits of both ends
+// of each listed edge, so that staging reads one contiguous record per entry.
+__global__ void k_prow_records(const int *pedge_ids, long long ME, const int *nxt, const float4 *vsplit, float4 *rec) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < ME;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int i = pedge_ids[e];
+        rec[2 * e] = vsplit[i];
+        rec[2 * e + 1] = vsplit[nxt[i]];
+    }
+}
+
+cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *nxt, const float4 *vsplit,
+                                float4 *rec, cudaStream_t s) {
+    k_prow_records<<<stream_blocks(ME, 256, 8192), 256, 0, s>>>(pedge_ids, ME, nxt, vsplit, rec);
+    return cudaGetLastError();
+}
+
 }  // namespace sj

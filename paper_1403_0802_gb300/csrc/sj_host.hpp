@@ -53,6 +53,7 @@ struct sj_layer {
     int *prow_r0 = nullptr;      // [nobj] first row of each polygon's MBB
     int *prow_start = nullptr;   // [MR + 1] list ranges in pedge_ids
     int *pedge_ids = nullptr;    // [ME] edge (= first vertex) indices
+    float4 *pedge_rec = nullptr; // [2 ME] FP32X staging records: vsplit of the edge's two ends
     unsigned long long *stats = nullptr;
     unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins

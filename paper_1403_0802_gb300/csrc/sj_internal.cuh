@@ -194,6 +194,7 @@ struct RefineArgs {
     const int *prow_r0;      //      [P] first grid row of each polygon's MBB
     const int *prow_start;   //      [slots + 1] edge list range of each (polygon, row)
     const int *pedge_ids;    //      edge (= first vertex) indices
+    const float4 *pedge_rec; //      [2 entries] vsplit of the entry's edge ends (FP32X staging)
     double D;                // P2P window
     float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
     float Df;                // D rounded to FP32 (staging prune)

@@ -50,7 +50,7 @@ struct PipSmem;
 
 template <>
 struct PipSmem<true> {
-    static constexpr int SMAX = 256;
+    static constexpr int SMAX = 128;
     float2 yh[SMAX];          // FP32 truncated y of the edge's two ends
     float4 rel[SMAX];         // cell-relative (ax, ay, bx, by)
     int vi[SMAX];             // global index of the edge's first end
@@ -269,10 +269,16 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
                 if (g < E) {
                     while (s.coff[kw + 1] <= g) ++kw;   // candidate of edge g (g grows by 32)
                     k = kw;
-                    i = a.pedge_ids[s.cvb[kw] + (g - s.coff[kw])];
-                    j = a.nxt[i];
-                    va = a.vsplit[i];
-                    vc = a.vsplit[j];
+                    const int e = s.cvb[kw] + (g - s.coff[kw]);
+                    i = a.pedge_ids[e];
+                    if constexpr (FP32) {
+                        va = a.pedge_rec[2 * (size_t)e];
+                        vc = a.pedge_rec[2 * (size_t)e + 1];
+                    } else {
+                        j = a.nxt[i];
+                        va = a.vsplit[i];
+                        vc = a.vsplit[j];
+                    }
                     keep = !(fmaxf(va.y, vc.y) < ylo || fminf(va.y, vc.y) > yhi);
                 }
                 const unsigned bal = __ballot_sync(FULL, keep);
