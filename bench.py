@@ -429,7 +429,9 @@ def run_ours(args):
 
 
 def run_serve(args):
-    """Continuous batching vs one join call per request on the same stream."""
+    """Continuous batching (native server, batched engine rounds) against one
+    join call per request in the same native loop -- in the same form and in
+    the plain FP64 form -- on one Poisson stream of requests."""
     import torch
     world, rank, local = dist_env()
     if rank != 0:
@@ -444,30 +446,36 @@ def run_serve(args):
     pool_p = torch.from_numpy(wp.points).pin_memory()
     pool_l = torch.from_numpy(wl.points).pin_memory()
     srv = serve.Server(pip, p2p, form=args.form, round_points=24_000_000, max_requests=4096)
-    # warm-up: workspaces, graphs, pools
-    warm = serve.make_stream(32, 0.0, pool_p, pool_l, seed=1)
-    srv.run(warm, mode="batched")
-    srv.run(serve.make_stream(8, 0.0, pool_p, pool_l, seed=2), mode="per_request")
-    # capacity of the per-request form at saturation sets the arrival rate
-    sat = srv.run(serve.make_stream(min(args.requests, 300), 0.0, pool_p, pool_l, seed=3), mode="per_request")
-    mean_pts = sat["points"] / sat["requests"]
+    arms = [("batched", args.form), ("per_request", args.form), ("per_request", "fp64")]
+    for mode, form in arms:      # warm-up: workspaces, graphs, allocator pools
+        srv.run(serve.make_stream(32, 0.0, pool_p, pool_l, seed=1), mode=mode, form=form)
+    # capacity of each arm with every request queued at t = 0
+    sat = {f"{m}_{f}": srv.run(serve.make_stream(min(args.requests, 300), 0.0, pool_p, pool_l, seed=3),
+                               mode=m, form=f) for m, f in arms}
+    mean_pts = sat[f"batched_{args.form}"]["points"] / sat[f"batched_{args.form}"]["requests"]
+    base = sat["per_request_fp64"]["points_per_s"]          # the plain FP64 one-launch-per-request form
     res = {}
     for rho in (0.5, 0.8):
-        rate = rho * sat["points_per_s"] / mean_pts
-        for mode in ("per_request", "batched"):
+        rate = rho * base / mean_pts
+        for m, f in arms:
             reqs = serve.make_stream(args.requests, rate, pool_p, pool_l, seed=7)
-            res[f"{mode}_rho{rho}"] = srv.run(reqs, mode=mode)
-    b, p = res["batched_rho0.8"], res["per_request_rho0.8"]
+            res[f"{m}_{f}_rho{rho}"] = srv.run(reqs, mode=m, form=f)
+    fast = sat[f"per_request_{args.form}"]["points_per_s"]  # a load the FP64 form cannot sustain
+    for m, f in arms[:2]:
+        reqs = serve.make_stream(args.requests, 0.8 * fast / mean_pts, pool_p, pool_l, seed=7)
+        res[f"{m}_{f}_rho0.8_of_{args.form}_capacity"] = srv.run(reqs, mode=m, form=f)
+    b, p64 = res[f"batched_{args.form}_rho0.8"], res["per_request_fp64_rho0.8"]
     line = {"metric": "serving p50/p99 latency (ms) and points/s, continuous batching", "value": b["p99_ms"],
-            "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests, "warmup": 40, "ms_per_step": b["mean_ms"],
+            "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests, "warmup": 32, "ms_per_step": b["mean_ms"],
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.form == "fp32x" else "f64", "data": "synthetic",
             "config": {"workload": f"serve_{args.requests}req_pip40k_p2p150k", "requests": args.requests,
                        "sizes": "log-uniform 1e3..5e6 points", "mix": "70% PIP / 30% P2P (D=100 m)",
-                       "arrivals": "Poisson, rate = rho x per-request capacity", "form": args.form},
+                       "arrivals": "Poisson, rate = rho x capacity of the plain FP64 one-join-per-request form",
+                       "form": args.form, "server": "native (sj_server_*), batched engine rounds"},
             "p50_ms": b["p50_ms"], "p99_ms": b["p99_ms"], "points_per_s": b["points_per_s"],
-            "per_request_p50_ms": p["p50_ms"], "per_request_p99_ms": p["p99_ms"],
-            "per_request_points_per_s": p["points_per_s"], "saturation_per_request": sat, "runs": res}
+            "plain_fp64_per_request_p50_ms": p64["p50_ms"], "plain_fp64_per_request_p99_ms": p64["p99_ms"],
+            "plain_fp64_per_request_points_per_s": p64["points_per_s"], "capacity": sat, "runs": res}
     print(json.dumps(line))
     srv.close()
     pip.close()

@@ -47,13 +47,25 @@ class sj_request(C.Structure):
                 ("out_d", C.c_void_p)]
 
 
+class sj_serve_request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("pts", C.c_void_p), ("n", C.c_int64),
+                ("out_id", C.c_void_p), ("out_d", C.c_void_p), ("not_before", C.c_double)]
+
+
+class sj_server_stats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("rounds", C.c_int64), ("points", C.c_int64),
+                ("max_launch_s", C.c_double), ("max_round_s", C.c_double)]
+
+
 SJ_OK, SJ_ERR_INVALID, SJ_ERR_OOM, SJ_ERR_GRID_COVER, SJ_ERR_CUDA, SJ_ERR_TIMEOUT, SJ_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
 SJ_FP64, SJ_FP32X = 0, 1
 SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
 SJ_FLAG_TIME_REFINE = 1
 SJ_FLAG_NO_GRAPH = 2
+SJ_SERVE_BATCHED, SJ_SERVE_PER_REQUEST = 0, 1
+SJ_SERVE_PIP, SJ_SERVE_P2P = 0, 1
 
-# name -> (restype, argtypes); every name here is declared in include/sj.h
+# name -> (restype, argtypes); every name here is declared in include/*.h
 _P, _I32, _I64, _D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
 _LP = C.POINTER(C.c_void_p)
 SIGNATURES = {
@@ -76,6 +88,16 @@ SIGNATURES = {
     "sj_engine_create": (C.c_int, [_I64, _I32, C.POINTER(sj_opts), _LP]),
     "sj_engine_round": (C.c_int, [_P, C.POINTER(sj_request), _I32, _P]),
     "sj_engine_destroy": (C.c_int, [_P]),
+    "sj_server_create": (C.c_int, [_P, _P, C.POINTER(sj_opts), _I32, _I64, _I64, _I32, _LP]),
+    "sj_server_submit": (C.c_int, [_P, C.POINTER(sj_serve_request), C.POINTER(C.c_int64)]),
+    "sj_server_wait": (C.c_int, [_P, _I64, C.POINTER(C.c_double)]),
+    "sj_server_poll": (C.c_int, [_P, _I64, C.POINTER(C.c_int32)]),
+    "sj_server_drain": (C.c_int, [_P]),
+    "sj_server_set_mode": (C.c_int, [_P, _I32, _I32]),
+    "sj_server_get_stats": (C.c_int, [_P, C.POINTER(sj_server_stats)]),
+    "sj_server_now": (C.c_double, [_P]),
+    "sj_server_reset_maxima": (C.c_int, [_P]),
+    "sj_server_destroy": (C.c_int, [_P]),
 }
 
 

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_build")
 SO = os.path.join(OUT, "libsj.so")
-SOURCES = ["sj_api.cu", "sj_engine.cu", "sj_filter.cu", "sj_pip.cu", "sj_p2p.cu", "sj_peaks.cu"]
+SOURCES = ["sj_api.cu", "sj_engine.cu", "sj_filter.cu", "sj_pip.cu", "sj_p2p.cu", "sj_peaks.cu", "sj_serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -84,3 +84,18 @@ def test_binding_imports_without_a_gpu():
 def test_request_struct_layout():
     from paper_1403_0802_gb300 import _lib
     assert C.sizeof(_lib.sj_request) == 40
+
+
+def test_server_struct_layouts_and_argument_checks(libsj):
+    """include/sj_serve.h: struct sizes, and argument errors reported without
+    touching a GPU."""
+    from paper_1403_0802_gb300 import _lib
+    assert C.sizeof(_lib.sj_serve_request) == 48
+    assert C.sizeof(_lib.sj_server_stats) == 48
+    lib = _lib.lib()
+    h = C.c_void_p()
+    assert lib.sj_server_create(None, None, None, 0, 1 << 20, 1000, 8, C.byref(h)) == _lib.SJ_ERR_INVALID
+    assert b"layer" in lib.sj_last_error()
+    t = C.c_int64()
+    assert lib.sj_server_submit(None, None, C.byref(t)) == _lib.SJ_ERR_INVALID
+    assert lib.sj_server_destroy(None) == _lib.SJ_OK

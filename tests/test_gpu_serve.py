@@ -31,25 +31,51 @@ def server():
     p2p.close()
 
 
-@pytest.mark.parametrize("mode", ["batched", "per_request"])
-def test_mix_equals_alone(server, mode):
+@pytest.mark.parametrize("mode,form", [("batched", None), ("per_request", None), ("per_request", "fp64")])
+def test_mix_equals_alone(server, mode, form):
     api, serve, srv, pool_p, pool_l = server
-    reqs = serve.make_stream(80, rate_per_s=4000.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=100,
+    # arrivals every ~5 us on average: requests arrive while others are on the GPU
+    reqs = serve.make_stream(80, rate_per_s=200_000.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=100,
                              size_max=60_000, seed=5)
-    stats = srv.run(reqs, mode=mode)
+    stats = srv.run(reqs, mode=mode, form=form)
     assert stats["requests"] == 80 and stats["p99_ms"] >= stats["p50_ms"] > 0
     if mode == "batched":
         assert stats["rounds"] < 80            # requests really shared rounds
+    form = form or srv.form
     for r in reqs:
         layer = srv.layers[r.kind]
         pts = r.pts.cuda()
         if r.kind == serve.PIP:
-            ref = api.pip_join(layer, pts, form=srv.form).cpu()
+            ref = api.pip_join(layer, pts, form=form).cpu()
             assert torch.equal(r.out_id, ref), r.rid
+        elif form == "fp64":                   # same arithmetic alone and in the mix: bit-exact
+            rid, rd = api.p2p_join(layer, pts, form=form)
+            assert torch.equal(r.out_id, rid.cpu()) and torch.equal(r.out_d, rd.cpu()), r.rid
         else:
-            rid, rd = api.p2p_join(layer, pts, form=srv.form)
+            rid, rd = api.p2p_join(layer, pts, form=form)
             a_id, a_d = r.out_id.numpy(), r.out_d.numpy()
             b_id, b_d = rid.cpu().numpy(), rd.cpu().numpy()
             assert (a_id == b_id).mean() > 0.999, r.rid
             both = (a_id >= 0) & (a_id == b_id)
             assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
+
+
+def test_arrivals_are_not_admitted_early(server):
+    """A request submitted with a future arrival time is not served before it
+    (its latency is measured from that arrival)."""
+    api, serve, srv, pool_p, pool_l = server
+    import ctypes as C
+    from paper_1403_0802_gb300 import _lib as L
+    lib = L.lib()
+    pts = pool_p[:1000].contiguous()
+    out = torch.empty(1000, dtype=torch.int32, pin_memory=True)
+    req = L.sj_serve_request(L.SJ_SERVE_PIP, 0, pts.data_ptr(), 1000, out.data_ptr(), None, 0.0)
+    t_arr = lib.sj_server_now(srv.handle) + 0.05
+    req.not_before = t_arr
+    tk, lat = C.c_int64(), C.c_double()
+    L.check(lib.sj_server_submit(srv.handle, C.byref(req), C.byref(tk)), "submit")
+    L.check(lib.sj_server_wait(srv.handle, tk.value, C.byref(lat)), "wait")
+    assert lib.sj_server_now(srv.handle) >= t_arr
+    assert 0.0 < lat.value < 0.05
+    ref = api.pip_join(srv.layers[serve.PIP], pts.cuda(), form=srv.form).cpu()
+    assert torch.equal(out, ref)
