@@ -322,6 +322,47 @@ def test_p2p_degenerate_polylines(api, oracle, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("D", [0.0, 50.0, 100.0])
+def test_p2p_window_across_cell_boundaries(api, oracle, form, D):
+    """Per-cell segment lists at their edges: axis-aligned segments on a 25 m
+    lattice (cells are 100 m, so segment ends and ends +- D fall on cell
+    boundaries), points at distance just under and just over D from a segment
+    end or side, in the neighbouring cells.  A segment missing from a cell's
+    list changes an id against the oracle, which filters whole polylines."""
+    rng = np.random.default_rng(int(D) + 11)
+    g = dict(x0=0.0, y0=0.0, x1=6400.0, y1=6400.0, nx=64, ny=64)
+    lines = []
+    for _ in range(400):
+        x, y = 25.0 * rng.integers(8, 248, 2)
+        k = int(rng.integers(1, 5))
+        if rng.random() < 0.5:
+            lines.append([(x, y), (x + 25.0 * k, y)])
+        else:
+            lines.append([(x, y), (x, y + 25.0 * k)])
+    verts = np.concatenate([np.asarray(l, np.float64) for l in lines])
+    off = np.arange(0, 2 * len(lines) + 1, 2, dtype=np.int64)
+    pts = []
+    for s_ in (1.0 - 1e-7, 1.0 + 1e-7):
+        r = D * s_
+        for (ax, ay), (bx, by) in lines:
+            for (px, py) in ((ax, ay), (bx, by), (0.5 * (ax + bx), 0.5 * (ay + by))):
+                for (ux, uy) in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    pts.append((px + r * ux, py + r * uy))
+                q = r / math.sqrt(2.0)
+                for (ux, uy) in ((1, 1), (1, -1), (-1, 1), (-1, -1)):
+                    pts.append((px + q * ux, py + q * uy))
+    pts = np.asarray(pts, np.float64)
+
+    class W:
+        pass
+    w = W()
+    w.grid, w.points, w.D, w.polylines = g, pts, D, None
+    with api.p2p_layer(verts, off, D, g) as layer:
+        gid, gd = api.p2p_join(layer, pts, form=form)
+    check_p2p(oracle, w, to_np(gid), to_np(gd), form, verts=verts, line_off=off)
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_host_buffers_match_device(api, oracle, form):
     w = synth.p2p_walks(n_points=50_000, n_lines=10_000)
     Lw = w.polylines
