@@ -161,6 +161,7 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.prow_start = L->prow_start;
     ra.pedge_ids = L->pedge_ids;
     ra.pedge_rec = L->pedge_rec;
+    ra.cand_cls = L->cand_cls;
     ra.D = L->D;
     ra.Df = L->Df;
     ra.Ddn = L->Ddn;
@@ -193,7 +194,7 @@ static void layer_free(sj_layer *L) {
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
                     L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
-                    L->prow_start, L->pedge_ids, L->pedge_rec};
+                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -365,6 +366,7 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
         CUDA_TRY(dalloc(&L->prow_start, 1));
         CUDA_TRY(dalloc(&L->pedge_ids, 0));
         CUDA_TRY(dalloc(&L->pedge_rec, 0));
+        CUDA_TRY(dalloc(&L->cand_cls, 0));
         CUDA_TRY(cudaMemsetAsync(L->prow_base, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(L->prow_start, 0, sizeof(int), s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -424,6 +426,12 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
                                    L->pedge_ids, s));
     CUDA_TRY(dalloc(&L->pedge_rec, 2 * (size_t)ME));
     if (ME > 0) CUDA_TRY(launch_prow_records(L->pedge_ids, (long long)ME, L->nxt, L->vsplit, L->pedge_rec, s));
+    // cell classes of the candidate entries; delta = 1e-7 of the largest grid
+    // coordinate (0.01 m at 1e5 m) is far above FP64 rounding and far below a cell
+    CUDA_TRY(dalloc(&L->cand_cls, (size_t)L->M));
+    if (L->M > 0)
+        CUDA_TRY(launch_pip_classify(L->g, L->cand_start, L->cand_ids, L->prow_base, L->prow_r0, L->prow_start,
+                                     L->pedge_ids, L->nxt, L->verts, 1e-7 * L->xmax + 1e-300, L->cand_cls, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
 }

@@ -54,6 +54,7 @@ struct sj_layer {
     int *prow_start = nullptr;   // [MR + 1] list ranges in pedge_ids
     int *pedge_ids = nullptr;    // [ME] edge (= first vertex) indices
     float4 *pedge_rec = nullptr; // [2 ME] FP32X staging records: vsplit of the edge's two ends
+    unsigned char *cand_cls = nullptr;   // [M] per candidate entry: 0 boundary, 1 inside, 2 outside
     unsigned long long *stats = nullptr;
     unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins

@@ -195,6 +195,8 @@ struct RefineArgs {
     const int *prow_start;   //      [slots + 1] edge list range of each (polygon, row)
     const int *pedge_ids;    //      edge (= first vertex) indices
     const float4 *pedge_rec; //      [2 entries] vsplit of the entry's edge ends (FP32X staging)
+    const unsigned char *cand_cls;   // PIP: per candidate entry 0 = boundary (test its edges),
+                                     //      1 = cell inside the polygon, 2 = outside
     double D;                // P2P window
     float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
     float Df;                // D rounded to FP32 (staging prune)
@@ -218,6 +220,11 @@ struct RefineArgs {
 __device__ __forceinline__ double2 slot_point(const RefineArgs &a, int j) {
     return a.spts ? a.spts[j] : a.pts[a.perm[j]];
 }
+
+// PIP cell classification (layer build): one class per candidate entry.
+cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
+                                const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
+                                const double2 *verts, double delta, unsigned char *cls, cudaStream_t s);
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);

@@ -14,8 +14,10 @@
 //      edge whose y-range lies strictly below ymin or strictly above ymax
 //      cannot straddle the horizontal line of any point of the item and is
 //      dropped (exact: its crossing count is 0 for every point; the test uses
-//      FP32 roundings that are monotone, with strict inequalities); the rest is
-//      compacted into shared memory with the lane's candidate index k.
+//      FP32 roundings that are monotone, with strict inequalities); so is an
+//      edge lying wholly left of every point of the item by a safe margin (a
+//      ray towards +x cannot cross it); the rest is compacted into shared
+//      memory with the lane's candidate index k.
 //   4. Whenever the staging area fills, the lanes split into point groups of
 //      SG lanes; each lane keeps a 32-bit parity mask (bit k = candidate k)
 //      over its strided share of the staged edges; the SG lanes XOR-fold their
@@ -34,6 +36,8 @@
 //             bound is redone in FP64 from the original vertices, so the result
 //             is the FP64 rule's, bit for bit.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "sj_internal.cuh"
 
@@ -199,8 +203,8 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
         const int row = c / a.g.nx;
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
-        // 1. points and the range of their FP32 y truncations
-        float ylo = FINF, yhi = -FINF;
+        // 1. points, the range of their FP32 y truncations and the smallest x truncation
+        float ylo = FINF, yhi = -FINF, xlo = FINF;
         for (int q = lane; q < np; q += 32) {
             const double2 p = slot_point(a, j0 + q);
             float hx, lx, hy, ly;
@@ -217,11 +221,13 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             s.par[q] = 0u;
             ylo = fminf(ylo, hy);
             yhi = fmaxf(yhi, hy);
+            xlo = fminf(xlo, hx);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ylo = fminf(ylo, __shfl_xor_sync(FULL, ylo, o));
             yhi = fmaxf(yhi, __shfl_xor_sync(FULL, yhi, o));
+            xlo = fminf(xlo, __shfl_xor_sync(FULL, xlo, o));
         }
         __syncwarp();
 
@@ -232,15 +238,19 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             if (pending == 0) break;
             // 2. candidate group: one polygon per lane, its edge list for the
             //    item's grid row, list lengths scanned
+            //    (a candidate whose class for this cell is inside / outside
+            //    contributes its parity without any edge)
             const int nc = min(32, k1 - kg);
-            int pid = 0, vb = 0, ne = 0, nall = 0;
+            int pid = 0, vb = 0, ne = 0, nall = 0, cls = 0;
             if (lane < nc) {
                 pid = a.cand_ids[kg + lane];
+                cls = a.cand_cls[kg + lane];
                 const int slot = a.prow_base[pid] + (row - a.prow_r0[pid]);
                 vb = a.prow_start[slot];
-                ne = a.prow_start[slot + 1] - vb;
+                ne = cls ? 0 : a.prow_start[slot + 1] - vb;
                 nall = a.obj_voff[pid + 1] - a.obj_voff[pid];
             }
+            const unsigned inside = __ballot_sync(FULL, cls == 1);
             c_pairs += (unsigned long long)pending * (unsigned long long)nc;
             c_algo += (unsigned long long)pending * (unsigned long long)__reduce_add_sync(FULL, (unsigned)nall);
             int incl = ne;
@@ -279,7 +289,16 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
                         va = a.vsplit[i];
                         vc = a.vsplit[j];
                     }
-                    keep = !(fmaxf(va.y, vc.y) < ylo || fminf(va.y, vc.y) > yhi);
+                    // y: strictly outside the points' y-range never straddles
+                    // (exact compares on monotone truncations).  x: an edge
+                    // wholly left of every point cannot cross a ray to +x; the
+                    // reference sign is a rounded FP64 orientation, so only
+                    // edges clear of the points by far more than its rounding
+                    // error (about 1e-10 m here) are dropped: a margin of 8
+                    // FP32 ulps plus 1 mm on the truncated coordinates.
+                    const float ex = fmaxf(va.x, vc.x);
+                    keep = !(fmaxf(va.y, vc.y) < ylo || fminf(va.y, vc.y) > yhi ||
+                             ex + fmaf(fabsf(ex) + fabsf(xlo), 9.5367431640625e-07f, 1e-3f) < xlo);
                 }
                 const unsigned bal = __ballot_sync(FULL, keep);
                 if (keep) {
@@ -305,7 +324,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             }
             // smallest candidate with odd parity
             for (int q = lane; q < np; q += 32) {
-                const unsigned m = s.par[q];
+                const unsigned m = s.par[q] | inside;
                 if (s.found[q] < 0 && m) s.found[q] = s.cid[__ffs(m) - 1];
                 s.par[q] = 0u;
             }
@@ -332,6 +351,61 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             atomicAdd(&a.stats[ST_HITS], (unsigned long long)c_hits);
         }
     }
+}
+
+// Cell classification (layer build), one warp per cell.  For a candidate P of
+// cell c, the only edges that can straddle the horizontal line of a point of c
+// are those of P's list for c's row.  If none of them meets the cell box
+// widened by delta, every point of the cell lies at least delta from each of
+// them, so (i) the straight path from the point to the cell centre crosses no
+// edge -- all points of the cell share the centre's inside/outside status --
+// and (ii) the FP64 crossing rule evaluates every such edge with the correct
+// orientation sign (its rounding error is below 1e-10 m at coordinates of
+// 1e5 m, delta is far larger), so the rule gives each point that status.  The
+// class is then the FP64 crossing parity of the centre: 1 inside, 2 outside;
+// 0 (boundary) when some edge meets the widened box.  The cell box is the
+// exact set of doubles the cell rule maps to the cell: [key_value(kx[ix]),
+// key_value(kx[ix + 1])) and likewise in y.
+__global__ void k_pip_classify(GridDev g, const int *cand_start, const int *cand_ids, const int *prow_base,
+                               const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
+                               const double2 *verts, double delta, unsigned char *cls) {
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int c = warp; c < g.G; c += nwarps) {
+        const int k0 = cand_start[c], k1 = cand_start[c + 1];
+        if (k0 == k1) continue;
+        const int ix = c % g.nx, iy = c / g.nx;
+        const double X0 = key_value(g.kx[ix]), X1 = key_value(g.kx[ix + 1]);
+        const double Y0 = key_value(g.ky[iy]), Y1 = key_value(g.ky[iy + 1]);
+        const double bx0 = X0 - delta, bx1 = X1 + delta, by0 = Y0 - delta, by1 = Y1 + delta;
+        const double cx = 0.5 * (X0 + X1), cy = 0.5 * (Y0 + Y1);
+        for (int k = k0; k < k1; ++k) {
+            const int P = cand_ids[k];
+            const int slot = prow_base[P] + (iy - prow_r0[P]);
+            const int e0 = prow_start[slot], e1 = prow_start[slot + 1];
+            int hit = 0, par = 0;
+            for (int e = e0 + lane; e < e1; e += 32) {
+                const int i = pedge_ids[e];
+                const double2 A = verts[i], B = verts[nxt[i]];
+                hit |= !(fmax(A.x, B.x) < bx0 || fmin(A.x, B.x) > bx1 || fmax(A.y, B.y) < by0 ||
+                         fmin(A.y, B.y) > by1);
+                par ^= cross64(cx, cy, A.x, A.y, B.x, B.y);
+            }
+            hit = __reduce_or_sync(FULL, (unsigned)hit);
+            par = (int)(__reduce_xor_sync(FULL, (unsigned)par) & 1u);
+            if (lane == 0) cls[k] = hit ? 0 : (par ? 1 : 2);
+        }
+    }
+}
+
+cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
+                                const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
+                                const double2 *verts, double delta, unsigned char *cls, cudaStream_t s) {
+    const long long nb = std::min<long long>(((long long)g.G * 32 + 255) / 256, 152LL * 64);
+    k_pip_classify<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(g, cand_start, cand_ids, prow_base, prow_r0,
+                                                                  prow_start, pedge_ids, nxt, verts, delta, cls);
+    return cudaGetLastError();
 }
 
 template <bool FP32>
