@@ -715,6 +715,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     fill_refine(L, ra);
     ra.items = b.items;
     ra.n_items = b.totals + 1;
+    ra.work_next = b.totals + 3;   // zeroed with the totals at the start of the join
     ra.cell_start = b.cell_start;
     ra.perm = b.perm;
     ra.spts = b.spts;

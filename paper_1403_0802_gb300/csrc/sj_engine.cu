@@ -210,6 +210,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     fill_refine(L, ra);
     ra.items = items;
     ra.n_items = totals + 1;
+    ra.work_next = totals + 3;     // zeroed with the totals at the start of each round
     ra.cell_start = cell_start;
     ra.perm = perm;
     ra.spts = spts;

@@ -193,7 +193,18 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
     unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0;
     unsigned c_fb = 0, c_hits = 0;
 
-    for (int it = blockIdx.x * PIP_WARPS + w; it < n_items; it += gridDim.x * PIP_WARPS) {
+    // Items come from a device counter when a.work_next is set (the next index
+    // is fetched at the start of an item, so its latency hides behind the
+    // item), else in a fixed stride.
+    int it = blockIdx.x * PIP_WARPS + w;
+    if (a.work_next) {
+        int t0 = 0;
+        if (lane == 0) t0 = atomicAdd(a.work_next, 1);
+        it = __shfl_sync(FULL, t0, 0);
+    }
+    while (it < n_items) {
+        int it_next = it + gridDim.x * PIP_WARPS;
+        if (a.work_next && lane == 0) it_next = atomicAdd(a.work_next, 1);
         ++c_items;
         const int2 item = a.items[it];
         const int c = item.x;
@@ -337,6 +348,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             if (f >= 0) ++c_hits;
         }
         __syncwarp();
+        it = a.work_next ? __shfl_sync(FULL, it_next, 0) : it_next;
     }
     if (a.stats) {
         c_fb = __reduce_add_sync(FULL, c_fb);
