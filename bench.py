@@ -445,7 +445,7 @@ def run_serve(args):
     p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
     pool_p = torch.from_numpy(wp.points).pin_memory()
     pool_l = torch.from_numpy(wl.points).pin_memory()
-    srv = serve.Server(pip, p2p, form=args.form, round_points=24_000_000, max_requests=4096)
+    srv = serve.Server(pip, p2p, form=args.form, round_points=6_000_000, max_requests=4096)
     arms = [("batched", args.form), ("per_request", args.form), ("per_request", "fp64")]
     for mode, form in arms:      # warm-up: workspaces, graphs, allocator pools
         srv.run(serve.make_stream(32, 0.0, pool_p, pool_l, seed=1), mode=mode, form=form)

@@ -176,9 +176,13 @@ sj_status sj_p2p_join(const sj_layer *layer, const double *pts, int64_t N, int32
                       const sj_opts *opts, void *stream);
 
 /* Same joins from HOST buffers: the library copies the points to the device,
- * joins, copies the results back, and synchronises `stream` before returning.
- * pts / out_id / out_d are host pointers (pinned memory gives overlap-free
- * full-bandwidth copies; pageable memory works too). */
+ * joins, copies the results back, and synchronises `stream` before returning
+ * (the work starts after what is already queued on `stream`).  Inputs of more
+ * than 2 M points are split into chunks joined in turn on two library-owned
+ * streams, so that copies in, joins and copies out of different chunks
+ * overlap; every point's result is the one sj_*_join gives.  pts / out_id /
+ * out_d are host pointers (pinned memory gives asynchronous full-bandwidth
+ * copies; pageable memory works too). */
 sj_status sj_pip_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id,
                            const sj_opts *opts, void *stream);
 sj_status sj_p2p_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,

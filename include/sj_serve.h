@@ -66,7 +66,9 @@ typedef struct {
     double max_round_s;   /* longest time from issuing a round to its completion  */
 } sj_server_stats;
 
-/* Create a server on the current device.  pip / p2p: resident layers (either
+/* Create a server on the current device (this also builds the engine's
+ * workspace and graph for each layer, so that no request waits for them).
+ * pip / p2p: resident layers (either
  * may be NULL if no request of that kind is submitted; they must outlive the
  * server).  opts: form and points per work item of every round (NULL = FP64,
  * defaults).  mode: SJ_SERVE_BATCHED or SJ_SERVE_PER_REQUEST.  hbm_budget:

@@ -87,6 +87,7 @@ sj_status sj::device_info(int dev, DevInfo **out) {
             uint64_t thr = UINT64_MAX;
             cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
         }
+        for (cudaStream_t &hs : d.hstream) CUDA_TRY(cudaStreamCreateWithFlags(&hs, cudaStreamNonBlocking));
         d.init = true;
     }
     *out = &d;
@@ -768,31 +769,72 @@ extern "C" sj_status sj_p2p_join(const sj_layer *L, const double *pts, int64_t N
     return join_impl(L, KIND_P2P, pts, N, out_id, out_d, o, stream);
 }
 
+// Host-buffer join, pipelined in three stages on library streams: chunks of
+// the points are copied in on one stream, joined on a second (each waiting for
+// its chunk's copy) and their results copied out on a third (each waiting for
+// its chunk's join), so that copies in, joins and copies out of different
+// chunks overlap (both copy directions and the SMs work at once).  Each chunk
+// is an independent join (a point's result does not depend on the other
+// points), so the outputs equal those of one join over all N points.
 static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                            const sj_opts *o, void *stream) {
     if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
     if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
+    if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (N == 0) return join_impl(L, kind, nullptr, 0, nullptr, nullptr, o, stream);
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DevInfo *di;
+    sj_status st = device_info(dev, &di);
+    if (st != SJ_OK) return st;
+    cudaStream_t t_in = di->hstream[0], t_cmp = di->hstream[1], t_out = di->hstream[2];
+    const int64_t CHUNK_MIN = 1 << 21;                       // 2 M points
+    const int64_t chunk = std::max<int64_t>(CHUNK_MIN, (N + 3) / 4);
+    const int nchunks = (int)((N + chunk - 1) / chunk);
     char *d = nullptr;
     size_t bp = (size_t)N * 16, bi = ((size_t)N * 4 + 255) & ~(size_t)255, bd = out_d ? (size_t)N * 8 : 0;
     CUDA_TRY(cudaMallocAsync((void **)&d, bp + bi + bd, s));
     double *dp = (double *)d;
-    int32_t *di = (int32_t *)(d + bp);
-    double *dd = out_d ? (double *)(d + bp + bi) : nullptr;
-    sj_status st = SJ_OK;
-    cudaError_t e = cudaMemcpyAsync(dp, pts, bp, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) {
-        st = join_impl(L, kind, dp, N, di, dd, o, stream);
-        if (st == SJ_OK) {
-            e = cudaMemcpyAsync(out_id, di, (size_t)N * 4, cudaMemcpyDeviceToHost, s);
-            if (e == cudaSuccess && out_d) e = cudaMemcpyAsync(out_d, dd, (size_t)N * 8, cudaMemcpyDeviceToHost, s);
-        }
+    int32_t *dI = (int32_t *)(d + bp);
+    double *dD = out_d ? (double *)(d + bp + bi) : nullptr;
+    std::vector<cudaEvent_t> evs(2 * (size_t)nchunks + 3, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &ev : evs)
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    cudaEvent_t ev_start = evs[0], ev_done = evs[1];
+    // every stage starts after the caller's stream (its prior work and the allocation)
+    if (e == cudaSuccess) e = cudaEventRecord(ev_start, s);
+    for (cudaStream_t t : {t_in, t_cmp, t_out})
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t, ev_start, 0);
+    for (int c = 0; c < nchunks && e == cudaSuccess && st == SJ_OK; ++c) {
+        cudaEvent_t copied = evs[2 + 2 * c], joined = evs[3 + 2 * c];
+        const int64_t off = (int64_t)c * chunk, n = std::min<int64_t>(chunk, N - off);
+        e = cudaMemcpyAsync(dp + 2 * off, pts + 2 * off, (size_t)n * 16, cudaMemcpyHostToDevice, t_in);
+        if (e == cudaSuccess) e = cudaEventRecord(copied, t_in);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t_cmp, copied, 0);
+        if (e != cudaSuccess) break;
+        st = join_impl(L, kind, dp + 2 * off, n, dI + off, dD ? dD + off : nullptr, o, t_cmp);
+        if (st != SJ_OK) break;
+        e = cudaEventRecord(joined, t_cmp);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(t_out, joined, 0);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(out_id + off, dI + off, (size_t)n * 4, cudaMemcpyDeviceToHost, t_out);
+        if (e == cudaSuccess && out_d)
+            e = cudaMemcpyAsync(out_d + off, dD + off, (size_t)n * 8, cudaMemcpyDeviceToHost, t_out);
     }
+    // the caller's stream waits for the join and copy-out stages (the copy-in
+    // stage is behind both), then frees the buffer
+    cudaError_t e2 = cudaEventRecord(ev_done, t_out);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, ev_done, 0);
+    if (e2 == cudaSuccess) e2 = cudaEventRecord(evs.back(), t_cmp);
+    if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, evs.back(), 0);
     cudaFreeAsync(d, s);
     cudaError_t e3 = cudaStreamSynchronize(s);
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     if (st != SJ_OK) return st;
     if (e != cudaSuccess) return cuda_fail(e, "host join copy");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "host join streams");
     if (e3 != cudaSuccess) return cuda_fail(e3, "cudaStreamSynchronize");
     return SJ_OK;
 }

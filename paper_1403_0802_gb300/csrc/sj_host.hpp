@@ -77,6 +77,7 @@ struct DevInfo {
     int sms = 0;
     int pip_bps[2] = {0, 0};
     int p2p_bps[2] = {0, 0};
+    cudaStream_t hstream[3] = {nullptr, nullptr, nullptr};   // host joins: copy in, join, copy out
     bool init = false;
 };
 

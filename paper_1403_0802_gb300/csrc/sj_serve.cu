@@ -449,6 +449,30 @@ extern "C" sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opt
     eo.pts_per_item = S->ppi;
     sj_status st = sj_engine_create(round_points, max_requests, &eo, &S->engine);
     if (st != SJ_OK) return undo(st);
+    // The engine builds a layer's workspace and captures its graph on the first
+    // round that uses the layer (allocations of hundreds of MB): do that now,
+    // with a one-point round per layer, so that no served request waits for it.
+    {
+        char *tmp = nullptr;
+        e = cudaMalloc((void **)&tmp, 256 * 3);
+        if (e != cudaSuccess) return undo(cuda_fail(e, "server warm-up"));
+        const double origin[2] = {0.0, 0.0};
+        e = cudaMemcpy(tmp, origin, sizeof(origin), cudaMemcpyHostToDevice);
+        for (int k = 0; k < 2 && e == cudaSuccess && st == SJ_OK; ++k) {
+            if (!S->layers[k]) continue;
+            sj_request r{};
+            r.layer = S->layers[k];
+            r.pts = (const double *)tmp;
+            r.N = 1;
+            r.out_id = (int32_t *)(tmp + 256);
+            r.out_d = k == 1 ? (double *)(tmp + 512) : nullptr;
+            st = sj_engine_round(S->engine, &r, 1, S->compute);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(S->compute);
+        cudaFree(tmp);
+        if (st != SJ_OK) return undo(st);
+        if (e != cudaSuccess) return undo(cuda_fail(e, "server warm-up"));
+    }
     S->worker = std::thread([S] { S->run(); });
     *out = S;
     return SJ_OK;

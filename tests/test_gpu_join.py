@@ -261,7 +261,7 @@ def test_layer_errors(api):
 @pytest.mark.parametrize("form", FORMS)
 def test_p2p_walks_full_size(api, oracle, form):
     """10,000,000 mixture points, 100,000 random-walk polylines, D = 100 m,
-    grid 1024 x 1024 -- the benchmark's workload and launch configuration."""
+    grid 512 x 512 -- the benchmark's workload and launch configuration."""
     w = synth.p2p_walks()
     Lw = w.polylines
     with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
@@ -378,6 +378,32 @@ def test_host_buffers_match_device(api, oracle, form):
                                       api.pip_join_host(layer, w.points, form=form))
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_host_join_pipelined_chunks(api, oracle, form):
+    """Host joins of more than 2 M points run as chunks on two streams; every
+    point's result equals the device join's (FP64 bit for bit; FP32X ids
+    equal and distances within the certified bound, since a point's FP64
+    recheck can depend on the other points of its work item)."""
+    w = synth.p2p_walks(n_points=5_000_001, n_lines=20_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        did, dd = api.p2p_join(layer, w.points, form=form)
+        hid, hd = api.p2p_join_host(layer, w.points, form=form)
+    did, dd = to_np(did), to_np(dd)
+    if form == "fp64":
+        np.testing.assert_array_equal(did, hid)
+        np.testing.assert_array_equal(dd, hd)
+    else:
+        assert (did == hid).mean() > 0.9999
+        both = (did >= 0) & (did == hid)
+        assert np.all(np.abs(dd[both] - hd[both]) <= 1e-3 * np.maximum(dd[both], 1.0))
+    w = synth.pip_stars(n_points=4_500_000)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        np.testing.assert_array_equal(to_np(api.pip_join(layer, w.points, form=form)),
+                                      api.pip_join_host(layer, w.points, form=form))
+
+
 def test_fp32x_fallback_rate_is_small(api, oracle):
     w = synth.p2p_walks(n_points=1_000_000)
     Lw = w.polylines
@@ -429,3 +455,51 @@ def test_pip_tiles_subset(api, oracle, form, layer):
     with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer_:
         got = to_np(api.pip_join(layer_, w.points, form=form))
     np.testing.assert_array_equal(got, ref)
+
+
+# ------------------------------------------------------------------ full-size at-scale configurations
+# The GPU joins every point, in the launch configuration bench.py times; the
+# oracle recomputes a seeded sample of the outputs one by one (it cannot join
+# 1e8 points in seconds).
+
+SAMPLE = 200_000
+
+
+@pytest.mark.parametrize("layer", [1, 2])
+def test_pip_at_scale_full_size_sampled(api, oracle, layer):
+    """100,000,000 clustered points against the 40,000-tile (layer 1) or the
+    heavy-tail 14,000-tile (layer 2) tiling, grid 1024 x 1024, FP32X: ids of
+    a 200,000-point sample bit-identical to the oracle; every point in exactly
+    one tile."""
+    w = synth.pip_tiles(layer=layer)
+    P = w.polygons
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer_:
+        pts = torch.as_tensor(w.points, device="cuda")
+        got = api.pip_join(layer_, pts, form="fp32x")
+        del pts
+        got = to_np(got)
+    assert (got >= 0).all()                              # a tiling covers the extent
+    idx = np.random.default_rng(layer).choice(len(w.points), SAMPLE, replace=False)
+    ref = oracle.pip_join(w.grid, np.ascontiguousarray(w.points[idx]), P.verts, P.ring_off, P.poly_ring_off)
+    np.testing.assert_array_equal(got[idx], ref)
+
+
+def test_p2p_at_scale_full_size_sampled(api, oracle):
+    """170,000,000 clustered points against 150,000 lognormal random walks,
+    D = 100 m, grid 512 x 512, FP32X: a 200,000-point sample against the
+    oracle (ids exact up to near-ties, distances within the certified bound)."""
+    w = synth.p2p_walks_lognormal()
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        pts = torch.as_tensor(w.points, device="cuda")
+        gid, gd = api.p2p_join(layer, pts, form="fp32x")
+        del pts
+        gid, gd = to_np(gid), to_np(gd)
+    idx = np.random.default_rng(4).choice(len(w.points), SAMPLE, replace=False)
+
+    class W:
+        pass
+    s = W()
+    s.grid, s.points, s.D, s.polylines = w.grid, np.ascontiguousarray(w.points[idx]), w.D, Lw
+    r = check_p2p(oracle, s, gid[idx], gd[idx], "fp32x")
+    assert 0.05 < r["hit_frac"] < 1.0
