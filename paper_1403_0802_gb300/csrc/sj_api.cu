@@ -775,7 +775,9 @@ extern "C" sj_status sj_p2p_join(const sj_layer *L, const double *pts, int64_t N
 // its chunk's join), so that copies in, joins and copies out of different
 // chunks overlap (both copy directions and the SMs work at once).  Each chunk
 // is an independent join (a point's result does not depend on the other
-// points), so the outputs equal those of one join over all N points.
+// points), so the outputs equal those of one join over all N points.  Two
+// chunks: every chunk is a full join with fixed costs (scans over every cell,
+// sparser work items), so four quarter joins were measured slower.
 static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                            const sj_opts *o, void *stream) {
     if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
@@ -790,7 +792,7 @@ static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64
     if (st != SJ_OK) return st;
     cudaStream_t t_in = di->hstream[0], t_cmp = di->hstream[1], t_out = di->hstream[2];
     const int64_t CHUNK_MIN = 1 << 21;                       // 2 M points
-    const int64_t chunk = std::max<int64_t>(CHUNK_MIN, (N + 3) / 4);
+    const int64_t chunk = std::max<int64_t>(CHUNK_MIN, (N + 1) / 2);
     const int nchunks = (int)((N + chunk - 1) / chunk);
     char *d = nullptr;
     size_t bp = (size_t)N * 16, bi = ((size_t)N * 4 + 255) & ~(size_t)255, bd = out_d ? (size_t)N * 8 : 0;
