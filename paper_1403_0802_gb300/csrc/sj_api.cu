@@ -19,7 +19,7 @@ cudaError_t launch_check_offsets(const int64_t *off, int64_t n, int64_t min_size
                                  int *bad, cudaStream_t s);
 cudaError_t launch_check_finite(const double2 *v, int n, int *bad, cudaStream_t s);
 cudaError_t launch_pip_topology(const int *ring_off, int R, const int *poly_ring_off, int P, int *poly_voff, int *nxt,
-                                cudaStream_t s);
+                                int *prv, cudaStream_t s);
 cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s);
 cudaError_t launch_seg_table(const double2 *v, const int *line_off, int L, double2 *e64, double *inv64, float4 *seg32,
                              cudaStream_t s);
@@ -43,6 +43,8 @@ cudaError_t launch_cseg_records(const int *cseg_start, const int *cseg_ids, cons
                                 cudaStream_t s);
 cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *nxt, const float4 *vsplit,
                                 float4 *rec, cudaStream_t s);
+cudaError_t launch_offsets(const int *cnt, int n, int *out, int2 *block_sums, size_t cap, int *totals,
+                           cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
@@ -163,6 +165,12 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.pedge_ids = L->pedge_ids;
     ra.pedge_rec = L->pedge_rec;
     ra.cand_cls = L->cand_cls;
+    ra.bnear_start = L->bnear_start;
+    ra.bnear_ids = L->bnear_ids;
+    ra.bnear_rec = L->bnear_rec;
+    ra.bflip_start = L->bflip_start;
+    ra.bflip_len = L->bflip_len;
+    ra.bflip_keys = L->bflip_keys;
     ra.D = L->D;
     ra.Df = L->Df;
     ra.Ddn = L->Ddn;
@@ -192,10 +200,11 @@ static void resolve_events(const sj_layer *L) {
 
 static void layer_free(sj_layer *L) {
     resolve_events(L);
-    void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->ring_off, L->poly_ring_off, L->seg_e64,
+    void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->prv, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
                     L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
-                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls};
+                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls, L->bnear_start, L->bnear_ids,
+                    L->bnear_rec, L->bflip_start, L->bflip_len, L->bflip_keys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -357,6 +366,73 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     return SJ_OK;
 }
 
+// PIP boundary entries (after the classes): near edge lists with staging
+// records, and the far-right parity flips (see k_pip_boundary).
+static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s) {
+    const int M = (int)L->M;
+    CUDA_TRY(dalloc(&L->bnear_start, (size_t)M + 1));
+    CUDA_TRY(dalloc(&L->bflip_start, (size_t)M + 1));
+    CUDA_TRY(dalloc(&L->bflip_len, (size_t)M));
+    if (M == 0) {
+        L->MN = L->MF = 0;
+        CUDA_TRY(dalloc(&L->bnear_ids, 0));
+        CUDA_TRY(dalloc(&L->bnear_rec, 0));
+        CUDA_TRY(dalloc(&L->bflip_keys, 0));
+        CUDA_TRY(cudaMemsetAsync(L->bnear_start, 0, sizeof(int), s));
+        CUDA_TRY(cudaMemsetAsync(L->bflip_start, 0, sizeof(int), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return SJ_OK;
+    }
+    struct Tmp {
+        void *p[5] = {};
+        ~Tmp() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } tmp;
+    BoundaryArgs a{};
+    a.g = L->g;
+    a.cand_start = L->cand_start;
+    a.cand_ids = L->cand_ids;
+    a.cls = L->cand_cls;
+    a.prow_base = L->prow_base;
+    a.prow_r0 = L->prow_r0;
+    a.prow_start = L->prow_start;
+    a.pedge_ids = L->pedge_ids;
+    a.nxt = L->nxt;
+    a.prv = L->prv;
+    a.verts = L->verts;
+    a.delta = delta;
+    int *totals = nullptr;
+    int2 *bs = nullptr;
+    const size_t cap = bucket_scan_blocks(M);
+    CUDA_TRY(dalloc(&a.near_cnt, (size_t)M)); tmp.p[0] = a.near_cnt;
+    CUDA_TRY(dalloc(&a.flip_cnt, (size_t)M)); tmp.p[1] = a.flip_cnt;
+    CUDA_TRY(dalloc(&totals, 8)); tmp.p[2] = totals;
+    CUDA_TRY(dalloc(&bs, cap)); tmp.p[3] = bs;
+    CUDA_TRY(launch_pip_boundary(a, 0, s));
+    CUDA_TRY(launch_offsets(a.near_cnt, M, L->bnear_start, bs, cap, totals, s));
+    CUDA_TRY(launch_offsets(a.flip_cnt, M, L->bflip_start, bs, cap, totals + 4, s));
+    int tot[8] = {};
+    CUDA_TRY(cudaMemcpyAsync(tot, totals, sizeof(tot), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    L->MN = tot[0];
+    L->MF = tot[4];
+    if (tot[0] < 0 || tot[4] < 0) return fail(SJ_ERR_INVALID, "boundary lists exceed 2^31 - 1 entries");
+    CUDA_TRY(dalloc(&L->bnear_ids, (size_t)L->MN));
+    CUDA_TRY(dalloc(&L->bnear_rec, 2 * (size_t)L->MN));
+    CUDA_TRY(dalloc(&L->bflip_keys, (size_t)L->MF));
+    a.near_start = L->bnear_start;
+    a.flip_start = L->bflip_start;
+    a.near_ids = L->bnear_ids;
+    a.flip_keys = L->bflip_keys;
+    CUDA_TRY(launch_pip_boundary(a, 1, s));
+    CUDA_TRY(launch_pip_flips(L->bflip_start, M, L->bflip_keys, L->bflip_len, s));
+    if (L->MN > 0) CUDA_TRY(launch_prow_records(L->bnear_ids, (long long)L->MN, L->nxt, L->vsplit, L->bnear_rec, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return SJ_OK;
+}
+
 // PIP per-(polygon, row) edge lists (after build_candidates).
 static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     const int P = L->nobj;
@@ -430,11 +506,12 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     // cell classes of the candidate entries; delta = 1e-7 of the largest grid
     // coordinate (0.01 m at 1e5 m) is far above FP64 rounding and far below a cell
     CUDA_TRY(dalloc(&L->cand_cls, (size_t)L->M));
+    const double delta = 1e-7 * L->xmax + 1e-300;
     if (L->M > 0)
         CUDA_TRY(launch_pip_classify(L->g, L->cand_start, L->cand_ids, L->prow_base, L->prow_r0, L->prow_start,
-                                     L->pedge_ids, L->nxt, L->verts, 1e-7 * L->xmax + 1e-300, L->cand_cls, s));
+                                     L->pedge_ids, L->nxt, L->verts, delta, L->cand_cls, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    return SJ_OK;
+    return build_boundary_lists(L, delta, s);
 }
 
 static sj_status layer_common_checks(const double *verts, int64_t V, const sj_grid *g, void *stream,
@@ -491,8 +568,9 @@ extern "C" sj_status sj_pip_layer_create(const double *verts, int64_t V, const i
     if (bad) return fail(SJ_ERR_INVALID, "invalid polygon layer (offsets, ring sizes or non-finite vertex)");
     CUDA_TRY(dalloc(&L->obj_voff, (size_t)P + 1));
     CUDA_TRY(dalloc(&L->nxt, (size_t)V));
+    CUDA_TRY(dalloc(&L->prv, (size_t)V));
     CUDA_TRY(dalloc(&L->vsplit, (size_t)V));
-    CUDA_TRY(launch_pip_topology(L->ring_off, (int)R, L->poly_ring_off, P, L->obj_voff, L->nxt, s));
+    CUDA_TRY(launch_pip_topology(L->ring_off, (int)R, L->poly_ring_off, P, L->obj_voff, L->nxt, L->prv, s));
     if (V > 0) CUDA_TRY(launch_split(L->verts, (int)V, L->vsplit, s));
     CUDA_TRY(dalloc(&L->stats, ST_N));
     CUDA_TRY(cudaMemsetAsync(L->stats, 0, sizeof(unsigned long long) * ST_N, s));

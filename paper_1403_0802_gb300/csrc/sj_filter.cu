@@ -393,11 +393,14 @@ __global__ void k_poly_voff(const int *ring_off, const int *poly_ring_off, int P
         poly_voff[p] = ring_off[poly_ring_off[p]];
 }
 
-// Next vertex within the same ring (closing edge wraps to the ring start).
-__global__ void k_ring_next(const int *ring_off, int R, int *nxt) {
+// Next and previous vertex within the same ring (the closing edge wraps).
+__global__ void k_ring_next(const int *ring_off, int R, int *nxt, int *prv) {
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
         int b = ring_off[r], e = ring_off[r + 1];
-        for (int i = b; i < e; ++i) nxt[i] = (i + 1 < e) ? i + 1 : b;
+        for (int i = b; i < e; ++i) {
+            nxt[i] = (i + 1 < e) ? i + 1 : b;
+            prv[i] = (i > b) ? i - 1 : e - 1;
+        }
     }
 }
 
@@ -722,9 +725,9 @@ cudaError_t launch_check_finite(const double2 *v, int n, int *bad, cudaStream_t 
     return cudaGetLastError();
 }
 cudaError_t launch_pip_topology(const int *ring_off, int R, const int *poly_ring_off, int P, int *poly_voff, int *nxt,
-                                cudaStream_t s) {
+                                int *prv, cudaStream_t s) {
     k_poly_voff<<<stream_blocks(P + 1, 256, 4096), 256, 0, s>>>(ring_off, poly_ring_off, P, poly_voff);
-    k_ring_next<<<stream_blocks(R, 128, 4096), 128, 0, s>>>(ring_off, R, nxt);
+    k_ring_next<<<stream_blocks(R, 128, 4096), 128, 0, s>>>(ring_off, R, nxt, prv);
     return cudaGetLastError();
 }
 cudaError_t launch_split(const double2 *v, int n, float4 *vs, cudaStream_t s) {
@@ -836,6 +839,13 @@ cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *n
                                 float4 *rec, cudaStream_t s) {
     k_prow_records<<<stream_blocks(ME, 256, 8192), 256, 0, s>>>(pedge_ids, ME, nxt, vsplit, rec);
     return cudaGetLastError();
+}
+
+// Exclusive offsets out[0..n] of the counts cnt[0..n) (out[n] = total, also in
+// totals[0]); block_sums holds cap entries (bucket_scan_blocks(n)).
+cudaError_t launch_offsets(const int *cnt, int n, int *out, int2 *block_sums, size_t cap, int *totals,
+                           cudaStream_t s) {
+    return run_scan(IntLoad{cnt}, OffsetApply{out}, n, block_sums, cap, totals, s);
 }
 
 }  // namespace sj

@@ -30,6 +30,7 @@ struct sj_layer {
     float4 *vsplit = nullptr;
     int *obj_voff = nullptr;
     int *nxt = nullptr;
+    int *prv = nullptr;        // PIP: previous vertex of the same ring
     int *ring_off = nullptr;
     int *poly_ring_off = nullptr;
     double2 *seg_e64 = nullptr;
@@ -55,6 +56,15 @@ struct sj_layer {
     int *pedge_ids = nullptr;    // [ME] edge (= first vertex) indices
     float4 *pedge_rec = nullptr; // [2 ME] FP32X staging records: vsplit of the edge's two ends
     unsigned char *cand_cls = nullptr;   // [M] per candidate entry: 0 boundary, 1 inside, 2 outside
+    // PIP boundary entries (class 0): near edges (x-range meets the cell's column
+    // widened by delta) and the flip keys of the far-right edges' parity in y
+    int64_t MN = 0, MF = 0;
+    int *bnear_start = nullptr;              // [M + 1]
+    int *bnear_ids = nullptr;                // [MN]
+    float4 *bnear_rec = nullptr;             // [2 MN] vsplit of both ends
+    int *bflip_start = nullptr;              // [M + 1]
+    int *bflip_len = nullptr;                // [M] keys left after cancelling equal pairs
+    unsigned long long *bflip_keys = nullptr;   // [MF] order keys, ascending within an entry
     unsigned long long *stats = nullptr;
     unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins

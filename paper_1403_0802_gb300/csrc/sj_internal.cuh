@@ -198,6 +198,12 @@ struct RefineArgs {
     const float4 *pedge_rec; //      [2 entries] vsplit of the entry's edge ends (FP32X staging)
     const unsigned char *cand_cls;   // PIP: per candidate entry 0 = boundary (test its edges),
                                      //      1 = cell inside the polygon, 2 = outside
+    const int *bnear_start;  // PIP boundary entries: near edge lists [M + 1]
+    const int *bnear_ids;
+    const float4 *bnear_rec; //      [2 per edge] vsplit of both ends
+    const int *bflip_start;  //      far-right parity flips: [M + 1] starts,
+    const int *bflip_len;    //      [M] lengths,
+    const unsigned long long *bflip_keys;   // ascending order keys of the flip y-values
     double D;                // P2P window
     float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
     float Df;                // D rounded to FP32 (staging prune)
@@ -221,6 +227,26 @@ struct RefineArgs {
 __device__ __forceinline__ double2 slot_point(const RefineArgs &a, int j) {
     return a.spts ? a.spts[j] : a.pts[a.perm[j]];
 }
+
+// Order key of a y-value with -0 folded onto +0 (IEEE compares treat them as
+// equal; the order key alone would not).
+__device__ __forceinline__ unsigned long long y_key(double v) { return order_key(v == 0.0 ? 0.0 : v); }
+
+// PIP boundary-entry lists (layer build): count (emit = 0) or emit (emit = 1).
+struct BoundaryArgs {
+    GridDev g;
+    const int *cand_start, *cand_ids;
+    const unsigned char *cls;
+    const int *prow_base, *prow_r0, *prow_start, *pedge_ids, *nxt, *prv;
+    const double2 *verts;
+    double delta;
+    int *near_cnt, *flip_cnt;                 // count pass: [M]
+    const int *near_start, *flip_start;       // emit pass
+    int *near_ids;
+    unsigned long long *flip_keys;
+};
+cudaError_t launch_pip_boundary(const BoundaryArgs &a, int emit, cudaStream_t s);
+cudaError_t launch_pip_flips(const int *flip_start, int M, unsigned long long *keys, int *len, cudaStream_t s);
 
 // PIP cell classification (layer build): one class per candidate entry.
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,

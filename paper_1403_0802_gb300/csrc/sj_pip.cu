@@ -251,17 +251,43 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
             //    item's grid row, list lengths scanned
             //    (a candidate whose class for this cell is inside / outside
             //    contributes its parity without any edge)
+            //    A boundary candidate stages only its near edges; the parity of
+            //    its far-right edges comes from the flip keys (k_pip_boundary).
             const int nc = min(32, k1 - kg);
-            int pid = 0, vb = 0, ne = 0, nall = 0, cls = 0;
+            int pid = 0, vb = 0, ne = 0, nall = 0, cls = 0, fs = 0, fl = 0;
             if (lane < nc) {
-                pid = a.cand_ids[kg + lane];
-                cls = a.cand_cls[kg + lane];
-                const int slot = a.prow_base[pid] + (row - a.prow_r0[pid]);
-                vb = a.prow_start[slot];
-                ne = cls ? 0 : a.prow_start[slot + 1] - vb;
+                const int k = kg + lane;
+                pid = a.cand_ids[k];
+                cls = a.cand_cls[k];
+                if (cls == 0) {
+                    vb = a.bnear_start[k];
+                    ne = a.bnear_start[k + 1] - vb;
+                    fs = a.bflip_start[k];
+                    fl = a.bflip_len[k];
+                }
                 nall = a.obj_voff[pid + 1] - a.obj_voff[pid];
             }
             const unsigned inside = __ballot_sync(FULL, cls == 1);
+            // far-right parity: the number of flip keys at or below the point's y
+            for (unsigned far = __ballot_sync(FULL, fl > 0); far; far &= far - 1) {
+                const int j = __ffs(far) - 1;
+                const int f0 = __shfl_sync(FULL, fs, j), n = __shfl_sync(FULL, fl, j);
+                for (int q = lane; q < np; q += 32) {
+                    if (s.found[q] >= 0) continue;
+                    double py;
+                    if constexpr (FP32) py = a.spts ? a.spts[s.pin[q]].y : a.pts[s.pin[q]].y;
+                    else py = s.pt[q].y;
+                    const unsigned long long ky = y_key(py);
+                    int lo = 0, hi = n;   // first key above ky
+                    while (lo < hi) {
+                        const int mid = (lo + hi) >> 1;
+                        if (a.bflip_keys[f0 + mid] <= ky) lo = mid + 1;
+                        else hi = mid;
+                    }
+                    if (lo & 1) s.par[q] ^= 1u << j;
+                }
+            }
+            __syncwarp();
             c_pairs += (unsigned long long)pending * (unsigned long long)nc;
             c_algo += (unsigned long long)pending * (unsigned long long)__reduce_add_sync(FULL, (unsigned)nall);
             int incl = ne;
@@ -291,10 +317,10 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
                     while (s.coff[kw + 1] <= g) ++kw;   // candidate of edge g (g grows by 32)
                     k = kw;
                     const int e = s.cvb[kw] + (g - s.coff[kw]);
-                    i = a.pedge_ids[e];
+                    i = a.bnear_ids[e];
                     if constexpr (FP32) {
-                        va = a.pedge_rec[2 * (size_t)e];
-                        vc = a.pedge_rec[2 * (size_t)e + 1];
+                        va = a.bnear_rec[2 * (size_t)e];
+                        vc = a.bnear_rec[2 * (size_t)e + 1];
                     } else {
                         j = a.nxt[i];
                         va = a.vsplit[i];
@@ -417,6 +443,135 @@ cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const i
     const long long nb = std::min<long long>(((long long)g.G * 32 + 255) / 256, 152LL * 64);
     k_pip_classify<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(g, cand_start, cand_ids, prow_base, prow_r0,
                                                                   prow_start, pedge_ids, nxt, verts, delta, cls);
+    return cudaGetLastError();
+}
+
+// Boundary entries (class 0), one warp per cell.  The candidate's row-list
+// edges split three ways against the cell's column [X0, X1) widened by delta:
+//   left  (max x < X0 - delta): farther than delta left of every point of the
+//         cell, so the FP64 rule never counts a crossing -- dropped;
+//   far   (min x > X1 + delta): farther than delta right of every point, so
+//         the FP64 rule counts a crossing exactly when the edge straddles the
+//         point's y (its orientation sign is far above rounding) -- the parity
+//         of those straddles is the parity of the number of end y-values
+//         (lower and upper end of each far edge) at or below the point's y,
+//         since an edge straddles y iff lower <= y < upper;
+//   near  (the rest): tested point by point in the refinement.
+// An end shared with the ring's adjacent edge counts twice when that edge is a
+// far edge of the same list too (the same vertex, the same y), which leaves
+// the parity unchanged: such ends are not emitted, so only the ends of chains
+// of far edges remain.
+// Count pass: near edges and far end values per entry.  Emit pass: near edge
+// ids and far end keys (order keys, -0 folded onto +0).
+__device__ __forceinline__ bool far_in_list(const BoundaryArgs &a, int u, int w, double XR, int iy) {
+    const double2 U = a.verts[u], W = a.verts[w];
+    if (!(fmin(U.x, W.x) > XR)) return false;
+    const int ra = clamped_axis(fmin(U.y, W.y), a.g.y0, a.g.ch, a.g.ny);
+    const int rb = clamped_axis(fmax(U.y, W.y), a.g.y0, a.g.ch, a.g.ny);
+    return ra <= iy && iy <= rb;
+}
+
+__global__ void k_pip_boundary(BoundaryArgs a, int emit) {
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int c = warp; c < a.g.G; c += nwarps) {
+        const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
+        if (k0 == k1) continue;
+        const int ix = c % a.g.nx, iy = c / a.g.nx;
+        const double XL = key_value(a.g.kx[ix]) - a.delta, XR = key_value(a.g.kx[ix + 1]) + a.delta;
+        for (int k = k0; k < k1; ++k) {
+            if (a.cls[k] != 0) {
+                if (!emit && lane == 0) a.near_cnt[k] = a.flip_cnt[k] = 0;
+                continue;
+            }
+            const int P = a.cand_ids[k];
+            const int slot = a.prow_base[P] + (iy - a.prow_r0[P]);
+            const int e0 = a.prow_start[slot], e1 = a.prow_start[slot + 1];
+            int nn = 0, nf = 0;   // running counts (uniform across the warp)
+            for (int b = e0; b < e1; b += 32) {
+                const int e = b + lane;
+                bool is_near = false, ks = false, ke = false;
+                int i = 0;
+                double ys = 0.0, ye = 0.0;
+                if (e < e1) {
+                    i = a.pedge_ids[e];
+                    const int j = a.nxt[i];
+                    const double2 A = a.verts[i], B = a.verts[j];
+                    const double xmin = fmin(A.x, B.x), xmax = fmax(A.x, B.x);
+                    const bool is_far = xmin > XR;
+                    is_near = !is_far && !(xmax < XL);
+                    if (is_far) {
+                        ks = !far_in_list(a, a.prv[i], i, XR, iy);   // start shared with the previous edge
+                        ke = !far_in_list(a, j, a.nxt[j], XR, iy);   // end shared with the next edge
+                    }
+                    ys = A.y;
+                    ye = B.y;
+                }
+                const unsigned bn = __ballot_sync(FULL, is_near);
+                const unsigned bs = __ballot_sync(FULL, ks), be = __ballot_sync(FULL, ke);
+                if (emit) {
+                    if (is_near) a.near_ids[a.near_start[k] + nn + __popc(bn & lt)] = i;
+                    const int f = a.flip_start[k] + nf + __popc(bs & lt) + __popc(be & lt);
+                    if (ks) a.flip_keys[f] = y_key(ys);
+                    if (ke) a.flip_keys[f + (ks ? 1 : 0)] = y_key(ye);
+                }
+                nn += __popc(bn);
+                nf += __popc(bs) + __popc(be);
+            }
+            if (!emit && lane == 0) {
+                a.near_cnt[k] = nn;
+                a.flip_cnt[k] = nf;
+            }
+        }
+    }
+}
+
+// Sort each entry's far end keys and drop pairs of equal keys (a value counted
+// twice does not change the parity); len[k] = the keys left.  One thread per
+// entry, Shell sort (Ciura gaps).
+__global__ void k_pip_flips(const int *flip_start, int M, unsigned long long *keys, int *len) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const int b = flip_start[k], n = flip_start[k + 1] - b;
+        unsigned long long *v = keys + b;
+        const int ciura[8] = {1, 4, 10, 23, 57, 132, 301, 701};
+        int gaps[32];
+        int ng = 0;
+        while (ng < 8 && ciura[ng] < n) { gaps[ng] = ciura[ng]; ++ng; }
+        if (ng == 8) {
+            long long g = 701;
+            while (ng < 32 && (g = g * 9 / 4) < n) gaps[ng++] = (int)g;
+        }
+        for (int u = ng - 1; u >= 0; --u) {
+            const int h = gaps[u];
+            for (int i = h; i < n; ++i) {
+                const unsigned long long x = v[i];
+                int j = i;
+                while (j >= h && v[j - h] > x) { v[j] = v[j - h]; j -= h; }
+                v[j] = x;
+            }
+        }
+        int m = 0;
+        for (int i = 0; i < n;) {   // runs of equal keys: keep one key of an odd run
+            int j = i + 1;
+            while (j < n && v[j] == v[i]) ++j;
+            if ((j - i) & 1) v[m++] = v[i];
+            i = j;
+        }
+        len[k] = m;
+    }
+}
+
+cudaError_t launch_pip_boundary(const BoundaryArgs &a, int emit, cudaStream_t s) {
+    const long long nb = std::min<long long>(((long long)a.g.G * 32 + 255) / 256, 152LL * 64);
+    k_pip_boundary<<<(int)std::max<long long>(nb, 1), 256, 0, s>>>(a, emit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pip_flips(const int *flip_start, int M, unsigned long long *keys, int *len, cudaStream_t s) {
+    const int nb = std::max(1, std::min((M + 127) / 128, 8192));
+    k_pip_flips<<<nb, 128, 0, s>>>(flip_start, M, keys, len);
     return cudaGetLastError();
 }
 
