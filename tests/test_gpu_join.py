@@ -363,6 +363,29 @@ def test_p2p_window_across_cell_boundaries(api, oracle, form, D):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_p2p_window_larger_than_the_extent(api, oracle, form):
+    """D larger than the grid's extent: every polyline is a candidate of every
+    cell and every segment is in every cell's list (the longest lists the
+    layer build sorts and the refinement stages)."""
+    rng = np.random.default_rng(17)
+    layer = synth.random_walks(rng, rng.integers(2, 41, size=800), extent=2048.0)
+    g = dict(x0=0.0, y0=0.0, x1=2048.0, y1=2048.0, nx=16, ny=16)
+    pts = rng.uniform(-100.0, 2148.0, (20_000, 2))
+
+    class W:
+        pass
+    w = W()
+    w.grid, w.points, w.D, w.polylines = g, pts, 3000.0, layer
+    with api.p2p_layer(layer.verts, layer.line_off, w.D, g) as L:
+        info = L.info()
+        assert info["n_candidates"] == 16 * 16 * 800
+        gid, gd = api.p2p_join(L, pts, form=form)
+    r = check_p2p(oracle, w, to_np(gid), to_np(gd), form)
+    inside = (pts[:, 0] >= 0) & (pts[:, 0] < 2048) & (pts[:, 1] >= 0) & (pts[:, 1] < 2048)
+    assert (to_np(gid)[inside] >= 0).all() and (to_np(gid)[~inside] < 0).all()
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_host_buffers_match_device(api, oracle, form):
     w = synth.p2p_walks(n_points=50_000, n_lines=10_000)
     Lw = w.polylines
