@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count")
     ap.add_argument("--form", choices=["fp32x", "fp64"], default="fp32x")
     ap.add_argument("--grid", type=int, default=0, help="filter grid cells per axis (0: the workload's)")
-    ap.add_argument("--ppi", type=int, default=0, help="points per work item, 1..128 (0: library default 64)")
+    ap.add_argument("--ppi", type=int, default=0, help="points per work item, 1..128 (0: library default 128)")
     ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64, e2e and CPU comparison legs")
     return ap.parse_args()
@@ -195,7 +195,7 @@ def metric_name(kind):
 
 def config_of(w, args):
     c = {"workload": w.name, "points": int(len(w.points)), "grid": f"{w.grid['nx']}x{w.grid['ny']}",
-         "form": args.form, "launch": "per_request", "pts_per_item": args.ppi or 64}
+         "form": args.form, "launch": "per_request", "pts_per_item": args.ppi or 128}
     big = len(w.points) * 16 > 129e6
     c["l2"] = ("inputs larger than L2 (points %d MB > 129 MB); no flush" % (len(w.points) * 16 // 10 ** 6) if big
                else "points %d MB fit in L2; steps re-read them (no flush)" % (len(w.points) * 16 // 10 ** 6))

@@ -82,7 +82,7 @@ typedef struct {
     int32_t form;            /* SJ_FP64 (default) or SJ_FP32X                       */
     int32_t launch;          /* SJ_PER_REQUEST (default) or SJ_PERSISTENT           */
     int32_t block;           /* threads per refinement block (multiple of 32), 0 = default */
-    int32_t pts_per_item;    /* points per work item, 1..128, 0 = default (64)     */
+    int32_t pts_per_item;    /* points per work item, 1..128, 0 = default (128)    */
     int32_t edges_per_chunk; /* reserved, 0                                         */
     int32_t flags;           /* SJ_FLAG_* bits                                      */
 } sj_opts;
@@ -178,9 +178,9 @@ sj_status sj_p2p_join(const sj_layer *layer, const double *pts, int64_t N, int32
 /* Same joins from HOST buffers: the library copies the points to the device,
  * joins, copies the results back, and synchronises `stream` before returning
  * (the work starts after what is already queued on `stream`).  Inputs of more
- * than 2 M points are split into two chunks, pipelined on three library-owned
- * streams (copy in, join, copy out), so that copies and joins of different
- * chunks overlap; every point's result is the one sj_*_join gives.  pts / out_id /
+ * than 2 M points are split into two or three chunks, pipelined on three
+ * library-owned streams (copy in, join, copy out), so that copies and joins of
+ * different chunks overlap; every point's result is the one sj_*_join gives.  pts / out_id /
  * out_d are host pointers (pinned memory gives asynchronous full-bandwidth
  * copies; pageable memory works too). */
 sj_status sj_pip_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id,

@@ -747,7 +747,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     if (launch != SJ_PER_REQUEST && launch != SJ_PERSISTENT) return fail(SJ_ERR_INVALID, "unknown launch form");
     if (form == SJ_FP32X && L->xmax > 1e30)
         return fail(SJ_ERR_INVALID, "SJ_FP32X needs grid coordinates below 1e30 in magnitude; use SJ_FP64");
-    int ch = (o && o->pts_per_item) ? o->pts_per_item : 64;
+    int ch = (o && o->pts_per_item) ? o->pts_per_item : 128;
     if (ch < 1 || ch > MAX_CH) return fail(SJ_ERR_INVALID, "pts_per_item must be in 1..128");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -853,9 +853,9 @@ extern "C" sj_status sj_p2p_join(const sj_layer *L, const double *pts, int64_t N
 // its chunk's join), so that copies in, joins and copies out of different
 // chunks overlap (both copy directions and the SMs work at once).  Each chunk
 // is an independent join (a point's result does not depend on the other
-// points), so the outputs equal those of one join over all N points.  Two
-// chunks: every chunk is a full join with fixed costs (scans over every cell,
-// sparser work items), so four quarter joins were measured slower.
+// points), so the outputs equal those of one join over all N points.  At most
+// three chunks: every chunk is a full join with fixed costs (scans over every
+// cell, sparser work items), so four quarter joins were measured slower.
 static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                            const sj_opts *o, void *stream) {
     if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
@@ -869,9 +869,19 @@ static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64
     sj_status st = device_info(dev, &di);
     if (st != SJ_OK) return st;
     cudaStream_t t_in = di->hstream[0], t_cmp = di->hstream[1], t_out = di->hstream[2];
-    const int64_t CHUNK_MIN = 1 << 21;                       // 2 M points
-    const int64_t chunk = std::max<int64_t>(CHUNK_MIN, (N + 1) / 2);
-    const int nchunks = (int)((N + chunk - 1) / chunk);
+    // chunk bounds: one chunk up to 2 M points, halves up to 8 M, else quarter /
+    // half / quarter (a short first chunk starts the joins early, a short last
+    // one keeps the final copy out short)
+    int64_t bound[4] = {0, N, N, N};
+    int nchunks = 1;
+    if (N > (int64_t)8 << 20) {
+        bound[1] = N / 4;
+        bound[2] = N - N / 4;
+        nchunks = 3;
+    } else if (N > (int64_t)2 << 20) {
+        bound[1] = N / 2;
+        nchunks = 2;
+    }
     char *d = nullptr;
     size_t bp = (size_t)N * 16, bi = ((size_t)N * 4 + 255) & ~(size_t)255, bd = out_d ? (size_t)N * 8 : 0;
     CUDA_TRY(cudaMallocAsync((void **)&d, bp + bi + bd, s));
@@ -889,7 +899,7 @@ static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64
         if (e == cudaSuccess) e = cudaStreamWaitEvent(t, ev_start, 0);
     for (int c = 0; c < nchunks && e == cudaSuccess && st == SJ_OK; ++c) {
         cudaEvent_t copied = evs[2 + 2 * c], joined = evs[3 + 2 * c];
-        const int64_t off = (int64_t)c * chunk, n = std::min<int64_t>(chunk, N - off);
+        const int64_t off = bound[c], n = bound[c + 1] - off;
         e = cudaMemcpyAsync(dp + 2 * off, pts + 2 * off, (size_t)n * 16, cudaMemcpyHostToDevice, t_in);
         if (e == cudaSuccess) e = cudaEventRecord(copied, t_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(t_cmp, copied, 0);

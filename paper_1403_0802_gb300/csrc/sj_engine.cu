@@ -265,7 +265,7 @@ extern "C" sj_status sj_engine_create(int64_t max_points, int32_t max_requests, 
     if (max_requests < 1 || max_requests > (1 << 20)) return fail(SJ_ERR_INVALID, "max_requests must be in 1..2^20");
     const int form = o ? o->form : SJ_FP64;
     if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
-    const int ch = (o && o->pts_per_item) ? o->pts_per_item : 64;
+    const int ch = (o && o->pts_per_item) ? o->pts_per_item : 128;
     if (ch < 1 || ch > MAX_CH) return fail(SJ_ERR_INVALID, "pts_per_item must be in 1..128");
     sj_engine *E = new sj_engine();
     cudaError_t e = cudaGetDevice(&E->device);

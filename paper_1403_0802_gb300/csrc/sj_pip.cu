@@ -211,7 +211,6 @@ __global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
         const int j0 = a.cell_start[c] + item.y;
         const int np = min(a.ch, a.cell_start[c + 1] - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
-        const int row = c / a.g.nx;
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
         // 1. points, the range of their FP32 y truncations and the smallest x truncation

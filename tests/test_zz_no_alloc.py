@@ -44,7 +44,9 @@ def test_noalloc_matches_allocating_join_twice_in_a_row(lib, walks, form):
         pts = torch.as_tensor(walks.points, device="cuda")
         batches = [pts, pts[170_000:].contiguous()]         # second call: another batch, leftover scratch
         for p in batches:
-            ref_id, ref_d = api.p2p_join(layer, p, form=form)
+            # same work items as the no-alloc join (64 points per item): the
+            # FP32X certification of a point depends on the other points of its item
+            ref_id, ref_d = api.p2p_join(layer, p, form=form, pts_per_item=64)
             out_id = torch.full((p.shape[0],), 7, dtype=torch.int32, device="cuda")
             out_d = torch.full((p.shape[0],), -1.0, dtype=torch.float64, device="cuda")
             api.p2p_join_noalloc(layer, p, out_id, out_d, form=form)
