@@ -304,11 +304,11 @@ def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE
     """PIP at scale: clustered points against a disjoint tiling.  Layer 1: 200 x 200
     tiles, side counts lognormal(median 2.6, sigma 1) capped at 1,250, three giant
     tiles (polygon median ~19, max ~5,000).  Layer 2: 140 x 100 tiles, side median
-    90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000).  Default
-    filter grid: 512 x 512 for layer 1, 1024 x 1024 for layer 2 (the faster of
-    512 / 1024 / 2048 per axis for each layer on GB300)."""
+    90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000).  Filter
+    grid 1024 x 1024 (the fastest of 512 / 1024 / 2048 per axis for both layers
+    at 100 M points on GB300)."""
     if grid_n is None:
-        grid_n = 512 if layer == 1 else 1024
+        grid_n = 1024
     rng = np.random.default_rng(seed + 10 * layer)
     if layer == 1:
         P = tiling(rng, 200, 200, side_median=2.6, side_cap=1250, n_giant=3)

@@ -79,3 +79,28 @@ def test_arrivals_are_not_admitted_early(server):
     assert 0.0 < lat.value < 0.05
     ref = api.pip_join(srv.layers[serve.PIP], pts.cuda(), form=srv.form).cpu()
     assert torch.equal(out, ref)
+
+
+def test_admission_waits_for_device_memory(server):
+    """A budget that holds only a couple of requests at a time: requests queue
+    until earlier ones release their arena blocks, every one completes, and the
+    results equal the joins alone."""
+    api, serve, srv, pool_p, pool_l = server
+    tight = serve.Server(srv.layers[serve.PIP], srv.layers[serve.P2P], form=srv.form, round_points=400_000,
+                         max_requests=64, hbm_budget=3_000_000)
+    try:
+        reqs = serve.make_stream(40, rate_per_s=0.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=20_000,
+                                 size_max=60_000, seed=9)
+        stats = tight.run(reqs, mode="batched")
+        assert stats["requests"] == 40
+        assert tight.stats()["completed"] == 40
+        for r in reqs:
+            pts = r.pts.cuda()
+            if r.kind == serve.PIP:
+                ref = api.pip_join(srv.layers[serve.PIP], pts, form=srv.form).cpu()
+                assert torch.equal(r.out_id, ref), r.rid
+            else:
+                rid, _ = api.p2p_join(srv.layers[serve.P2P], pts, form=srv.form)
+                assert (r.out_id.numpy() == rid.cpu().numpy()).mean() > 0.999, r.rid
+    finally:
+        tight.close()
