@@ -216,20 +216,28 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
     // Items come from a device counter when a.work_next is set (the next index
     // is fetched at the start of an item, so its latency hides behind the
     // item), else in a fixed stride.
+    // The next item's record and its cell's point range are loaded while the
+    // current item is refined, off the per-item chain of dependent loads.
     int it = blockIdx.x * P2P_WARPS + w;
     if (a.work_next) {
         int t0 = 0;
         if (lane == 0) t0 = atomicAdd(a.work_next, 1);
         it = __shfl_sync(FULL, t0, 0);
     }
+    int2 item = make_int2(0, 0);
+    int cs0 = 0, cs1 = 0;
+    if (it < n_items) {
+        item = a.items[it];
+        cs0 = a.cell_start[item.x];
+        cs1 = a.cell_start[item.x + 1];
+    }
     while (it < n_items) {
         int it_next = it + gridDim.x * P2P_WARPS;
         if (a.work_next && lane == 0) it_next = atomicAdd(a.work_next, 1);
         ++c_items;
-        const int2 item = a.items[it];
         const int c = item.x;
-        const int j0 = a.cell_start[c] + item.y;
-        const int np = min(a.ch, a.cell_start[c + 1] - j0);
+        const int j0 = cs0 + item.y;
+        const int np = min(a.ch, cs1 - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
@@ -253,6 +261,9 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         bxlo = warp_min(bxlo); bylo = warp_min(bylo);
         bxhi = warp_max(bxhi); byhi = warp_max(byhi);
         pmag = warp_max(pmag);
+        if (a.work_next) it_next = __shfl_sync(FULL, it_next, 0);
+        int2 item_n = make_int2(0, 0);
+        if (it_next < n_items) item_n = a.items[it_next];
         float mag = pmag;   // FP32X: largest |cell-relative coordinate| refined for this item
         c_pairs += (unsigned long long)np * (unsigned long long)(k1 - k0);
         c_algo += (unsigned long long)np * (unsigned long long)a.cell_algo[c];
@@ -308,6 +319,11 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                 nst = 0;
             }
         }
+        int cs0n = 0, cs1n = 0;
+        if (it_next < n_items) {
+            cs0n = a.cell_start[item_n.x];
+            cs1n = a.cell_start[item_n.x + 1];
+        }
         if constexpr (FP32) mag = warp_max(mag);
         for (int q = lane; q < np; q += 32) {
             const int id = s.i1[q];
@@ -356,7 +372,10 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             if (out >= 0) ++c_hits;
         }
         __syncwarp();
-        it = a.work_next ? __shfl_sync(FULL, it_next, 0) : it_next;
+        it = it_next;
+        item = item_n;
+        cs0 = cs0n;
+        cs1 = cs1n;
     }
     if (a.stats) {
         c_fb = __reduce_add_sync(FULL, c_fb);
