@@ -334,7 +334,8 @@ def roofline_of(w, form, st, props, peaks):
     join's stream.  Work per launch = the (point, edge or segment) tests the
     kernel executes (the candidate lists' tests minus the exact staging prune)
     x the algorithmic FP ops of one test; achieved = that / launch time.  The
-    unpruned count (SURVEY 8(d) units) is reported as effective_tflops."""
+    unpruned count (points x segments or edges of the candidate objects) is
+    reported as effective_tflops."""
     refine_ms = st["refine_ms"] / max(st["refine_launches"], 1)
     joins = max(st["joins"], 1)
     algo = st["algo_tests"] / joins
