@@ -468,6 +468,14 @@ extern "C" sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opt
             r.out_d = k == 1 ? (double *)(tmp + 512) : nullptr;
             st = sj_engine_round(S->engine, &r, 1, S->compute);
         }
+        // Direct joins take their scratch from the stream-ordered pool (which
+        // keeps freed memory): reserve the largest one now (a request of
+        // round_points points needs under 64 B per point plus per-cell arrays)
+        // so that the pool never grows while requests are served.
+        void *big = nullptr;
+        if (e == cudaSuccess)
+            e = cudaMallocAsync(&big, (size_t)round_points * 64 + ((size_t)64 << 20), S->compute);
+        if (e == cudaSuccess) e = cudaFreeAsync(big, S->compute);
         if (e == cudaSuccess) e = cudaStreamSynchronize(S->compute);
         cudaFree(tmp);
         if (st != SJ_OK) return undo(st);
