@@ -175,6 +175,17 @@ sj_status sj_pip_join(const sj_layer *layer, const double *pts, int64_t N, int32
 sj_status sj_p2p_join(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                       const sj_opts *opts, void *stream);
 
+/* sj_p2p_join with a window chosen per call (Sec. III.B fixes the distance D
+ * when the polylines are indexed; this entry point answers any smaller
+ * distance query on the same resident layer): the nearest polyline within
+ * `window` instead of the layer's D, with the same outputs, precision and
+ * streams as sj_p2p_join.  The layer's grid lists, built for D, stay valid for
+ * every window <= D; a smaller window prunes no more cells, so the call costs
+ * what sj_p2p_join costs.  Errors: SJ_ERR_INVALID when window is NaN, negative
+ * or larger than the layer's D. */
+sj_status sj_p2p_join_window(const sj_layer *layer, const double *pts, int64_t N, double window, int32_t *out_id,
+                             double *out_d, const sj_opts *opts, void *stream);
+
 /* Same joins from HOST buffers: the library copies the points to the device,
  * joins, copies the results back, and synchronises `stream` before returning
  * (the work starts after what is already queued on `stream`).  Inputs of more
@@ -220,6 +231,10 @@ typedef struct {
     int64_t N;
     int32_t *out_id;         /* dev [N] int32                                     */
     double *out_d;           /* dev [N] f64 for polyline layers (may be NULL)     */
+    int32_t use_window;      /* polyline layers: nonzero = join within `window`
+                                (as sj_p2p_join_window); 0 = the layer's D        */
+    int32_t pad;
+    double window;           /* 0 <= window <= the layer's D when use_window      */
 } sj_request;
 
 /* opts.flags for sj_engine_create: launch the round's kernels directly instead
@@ -229,8 +244,8 @@ typedef struct {
 /* Create an engine for rounds of at most max_points points and max_requests
  * requests per layer.  opts selects form and points per work item (as for the
  * joins; NULL = defaults).  The engine allocates one workspace per layer on
- * the first round that uses the layer (about 52 bytes per point plus 8 bytes
- * per grid cell) and captures that layer's graph then; later rounds allocate
+ * the first round that uses the layer (about 36 bytes per point for a
+ * polygon layer, 60 for a polyline layer, plus 8 bytes per grid cell) and captures that layer's graph then; later rounds allocate
  * nothing.  Layers must outlive the engine.  Errors: SJ_ERR_INVALID. */
 sj_status sj_engine_create(int64_t max_points, int32_t max_requests, const sj_opts *opts, sj_engine **out);
 
@@ -238,8 +253,12 @@ sj_status sj_engine_create(int64_t max_points, int32_t max_requests, const sj_op
  * needed for graph replay; the legacy stream runs the kernels directly).  The
  * host blocks only if the request table of the round-before-last for the same
  * layer has not been copied to the device yet.  Rounds on one engine must be
- * issued on one stream (or ordered by the caller).  Errors: SJ_ERR_INVALID
- * (sizes beyond the engine's limits, bad buffers), SJ_ERR_CUDA, SJ_ERR_OOM. */
+ * issued on one stream (or ordered by the caller).  Requests against one
+ * polyline layer may ask for different windows: each point is joined within
+ * its request's window (a round with windows below D also writes one window
+ * per point, 8 bytes).  Errors: SJ_ERR_INVALID (sizes beyond the engine's
+ * limits, bad buffers, a window outside [0, D] or on a polygon layer),
+ * SJ_ERR_CUDA, SJ_ERR_OOM. */
 sj_status sj_engine_round(sj_engine *engine, const sj_request *reqs, int32_t n, void *stream);
 
 /* Free the engine (synchronises the device first).  NULL is a no-op. */

@@ -47,7 +47,8 @@ enum { SJ_SERVE_PIP = 0, SJ_SERVE_P2P = 1 };
  * int32; out_d: [n] float64 for P2P (may be NULL; ignored for PIP). */
 typedef struct {
     int32_t kind;         /* SJ_SERVE_PIP or SJ_SERVE_P2P                        */
-    int32_t pad;
+    int32_t use_window;   /* P2P: nonzero = join within `window` instead of the
+                             layer's D (as sj_p2p_join_window)                    */
     const double *pts;
     int64_t n;            /* 1 .. round_points                                    */
     int32_t *out_id;
@@ -55,6 +56,7 @@ typedef struct {
     double not_before;    /* server clock (sj_server_now), seconds: the request
                              arrives then and is not admitted earlier; 0 = now.
                              Requests must be submitted in not_before order.      */
+    double window;        /* 0 <= window <= the P2P layer's D when use_window     */
 } sj_serve_request;
 
 typedef struct {
@@ -82,7 +84,8 @@ sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opts *opts, in
 /* Queue a request (thread-safe, does not block on the GPU).  *ticket receives
  * its id for sj_server_wait / sj_server_poll.  Errors: SJ_ERR_INVALID (bad
  * kind, missing layer, n out of range, NULL buffers, a request larger than
- * the device budget), or the error that stopped the worker. */
+ * the device budget, a window outside [0, D] or on a PIP request), or the
+ * error that stopped the worker. */
 sj_status sj_server_submit(sj_server *s, const sj_serve_request *req, int64_t *ticket);
 
 /* Block until request `ticket` is done; *latency_s (may be NULL) receives

@@ -44,12 +44,12 @@ class sj_peak_rates(C.Structure):
 
 class sj_request(C.Structure):
     _fields_ = [("layer", C.c_void_p), ("pts", C.c_void_p), ("N", C.c_int64), ("out_id", C.c_void_p),
-                ("out_d", C.c_void_p)]
+                ("out_d", C.c_void_p), ("use_window", C.c_int32), ("pad", C.c_int32), ("window", C.c_double)]
 
 
 class sj_serve_request(C.Structure):
-    _fields_ = [("kind", C.c_int32), ("pad", C.c_int32), ("pts", C.c_void_p), ("n", C.c_int64),
-                ("out_id", C.c_void_p), ("out_d", C.c_void_p), ("not_before", C.c_double)]
+    _fields_ = [("kind", C.c_int32), ("use_window", C.c_int32), ("pts", C.c_void_p), ("n", C.c_int64),
+                ("out_id", C.c_void_p), ("out_d", C.c_void_p), ("not_before", C.c_double), ("window", C.c_double)]
 
 
 class sj_server_stats(C.Structure):
@@ -76,6 +76,7 @@ SIGNATURES = {
     "sj_layer_get_candidates": (C.c_int, [_P, _P, _P]),
     "sj_pip_join": (C.c_int, [_P, _P, _I64, _P, C.POINTER(sj_opts), _P]),
     "sj_p2p_join": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
+    "sj_p2p_join_window": (C.c_int, [_P, _P, _I64, C.c_double, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_pip_join_host": (C.c_int, [_P, _P, _I64, _P, C.POINTER(sj_opts), _P]),
     "sj_p2p_join_host": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_p2p_join_noalloc": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),

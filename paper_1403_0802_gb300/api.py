@@ -146,15 +146,20 @@ def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp
 
 def p2p_join(layer: Layer, pts, out_id: torch.Tensor | None = None, out_d: torch.Tensor | None = None,
              form: str = "fp64", launch: str = "per_request", pts_per_item: int = 0, stream=None,
-             time_refine: bool = False):
-    """(nearest polyline id or -1, distance or +inf) per point (Sec. III.B)."""
+             time_refine: bool = False, window: float | None = None):
+    """(nearest polyline id or -1, distance or +inf) per point (Sec. III.B); window (<= the layer's D)
+    replaces D for this call (sj_p2p_join_window)."""
     p = _points(pts)
     n = p.shape[0]
     out_id = torch.empty(n, dtype=torch.int32, device=p.device) if out_id is None else out_id
     out_d = torch.empty(n, dtype=torch.float64, device=p.device) if out_d is None else out_d
     o = _opts(form, launch, pts_per_item, time_refine)
-    L.check(L.lib().sj_p2p_join(layer.handle, _ptr(p), n, _ptr(out_id), _ptr(out_d), C.byref(o), _stream(stream)),
-            "sj_p2p_join")
+    if window is None:
+        L.check(L.lib().sj_p2p_join(layer.handle, _ptr(p), n, _ptr(out_id), _ptr(out_d), C.byref(o),
+                                    _stream(stream)), "sj_p2p_join")
+    else:
+        L.check(L.lib().sj_p2p_join_window(layer.handle, _ptr(p), n, float(window), _ptr(out_id), _ptr(out_d),
+                                           C.byref(o), _stream(stream)), "sj_p2p_join_window")
     return out_id, out_d
 
 
@@ -235,7 +240,9 @@ class Engine:
         eng.round([(pip_layer, pts_a, ids_a, None), (p2p_layer, pts_b, ids_b, d_b)], stream)
 
     Each request is (layer, points [N, 2] f64 CUDA tensor, out_id int32 [N],
-    out_d f64 [N] or None); outputs are written asynchronously on `stream`.
+    out_d f64 [N] or None[, window]); outputs are written asynchronously on
+    `stream`.  A window (polyline layers, <= the layer's D) replaces D for that
+    request alone.
     """
 
     def __init__(self, max_points: int, max_requests: int = 1024, form: str = "fp64", pts_per_item: int = 0,
@@ -251,9 +258,12 @@ class Engine:
 
     def round(self, requests, stream=None):
         arr = (L.sj_request * max(len(requests), 1))()
-        for k, (layer, pts, out_id, out_d) in enumerate(requests):
+        for k, req in enumerate(requests):
+            layer, pts, out_id, out_d = req[:4]
+            window = req[4] if len(req) > 4 else None
             arr[k] = L.sj_request(layer.handle.value, _ptr(pts), pts.shape[0], _ptr(out_id),
-                                  _ptr(out_d) if out_d is not None else None)
+                                  _ptr(out_d) if out_d is not None else None, 0 if window is None else 1, 0,
+                                  0.0 if window is None else float(window))
         L.check(L.lib().sj_engine_round(self._h, arr, len(requests), _stream(stream)), "sj_engine_round")
 
     def close(self):

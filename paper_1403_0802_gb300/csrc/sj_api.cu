@@ -734,10 +734,14 @@ static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_f
     b.resd = res == RES_D ? s.take<ResD>((size_t)N) : nullptr;
 }
 
+// window < 0: the layer's D; else a P2P window 0 <= window <= D for this call
+// alone (the layer's lists, built for D, hold every segment within any smaller
+// window, so the same kernels apply with the window's thresholds).
 static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
-                           const sj_opts *o, void *stream) {
+                           const sj_opts *o, void *stream, double window = -1.0) {
     if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
     if (L->kind != kind) return fail(SJ_ERR_INVALID, kind == KIND_PIP ? "not a polygon layer" : "not a polyline layer");
+    if (window >= 0.0 && !(window <= L->D)) return fail(SJ_ERR_INVALID, "window must lie in [0, layer D]");
     if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
     if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
     if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
@@ -792,6 +796,12 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
 
     RefineArgs ra{};
     fill_refine(L, ra);
+    if (window >= 0.0) {
+        ra.D = window;
+        ra.Df = (float)window;
+        ra.Ddn = float_down(window * (1.0 - 1e-12));
+        ra.Dup = float_up(window * (1.0 + 1e-12) + 1e-300);
+    }
     ra.items = b.items;
     ra.n_items = b.totals + 1;
     ra.work_next = b.totals + 3;   // zeroed with the totals at the start of the join
@@ -845,6 +855,12 @@ extern "C" sj_status sj_pip_join(const sj_layer *L, const double *pts, int64_t N
 extern "C" sj_status sj_p2p_join(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                                  const sj_opts *o, void *stream) {
     return join_impl(L, KIND_P2P, pts, N, out_id, out_d, o, stream);
+}
+
+extern "C" sj_status sj_p2p_join_window(const sj_layer *L, const double *pts, int64_t N, double window,
+                                        int32_t *out_id, double *out_d, const sj_opts *o, void *stream) {
+    if (!(window >= 0.0)) return fail(SJ_ERR_INVALID, "window must lie in [0, layer D]");   // NaN too
+    return join_impl(L, KIND_P2P, pts, N, out_id, out_d, o, stream, window);
 }
 
 // Host-buffer join, pipelined in three stages on library streams: chunks of

@@ -34,14 +34,15 @@ struct ReqDev {
     const double2 *pts;
     int *out_id;
     double *out_d;
-    int off;   // first global point index
+    double window;   // P2P window of this request (the layer's D when none is asked)
+    int off;         // first global point index
     int n;
 };
 
 struct MultiArgs {
     GridDev g;
     const ReqDev *reqs;
-    const int *meta;       // [0] number of requests, [1] total points
+    const int *meta;       // [0] number of requests, [1] total points, [2] per-request windows on
     int *cnt;
     int2 *key_rank;
     int *pos;
@@ -50,6 +51,7 @@ struct MultiArgs {
     double2 *spts;
     int *res_id;           // cell-ordered results (refinement writes the points of work items)
     double *res_d;
+    double *win;           // P2P: per-slot window, written when meta[2] != 0
 };
 
 // Request owning global point i: the last request whose offset is <= i.
@@ -78,6 +80,7 @@ __global__ void k_cell_hist_multi(MultiArgs m) {
 // without candidates belong to no work item and keep that result.
 __global__ void k_scatter_multi(MultiArgs m) {
     const int nr = m.meta[0], total = m.meta[1];
+    const bool pw = m.win && m.meta[2];
     const double INF = __longlong_as_double(0x7ff0000000000000LL);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
         const int2 k = m.key_rank[i];
@@ -89,6 +92,7 @@ __global__ void k_scatter_multi(MultiArgs m) {
             m.spts[q] = R.pts[i - R.off];
             m.res_id[q] = -1;
             if (m.res_d) m.res_d[q] = INF;
+            if (pw) m.win[q] = R.window;
         }
         m.pos[i] = q;
     }
@@ -167,7 +171,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     int *cnt, *cell_start, *totals, *pos, *perm, *res_id;
     int2 *key_rank, *items, *block_sums, *fb;
     double2 *spts;
-    double *res_d;
+    double *res_d, *win;
     auto lay = [&](Scratch &x) {
         cnt = x.take<int>((size_t)G + 1);
         cell_start = x.take<int>((size_t)G + 1);
@@ -180,6 +184,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
         block_sums = x.take<int2>(bucket_scan_blocks(G));
         res_id = x.take<int>((size_t)N);
         res_d = p2p ? x.take<double>((size_t)N) : nullptr;
+        win = p2p ? x.take<double>((size_t)N) : nullptr;
         fb = (p2p && E->form == SJ_FP32X) ? x.take<int2>((size_t)N) : nullptr;
         w->d_reqs = x.take<ReqDev>((size_t)E->max_requests);
         w->d_meta = x.take<int>(4);
@@ -219,6 +224,8 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     ra.res_d = res_d;
     ra.fb = fb;
     ra.n_fb = totals + 2;
+    ra.win = win;
+    ra.win_on = p2p ? w->d_meta + 2 : nullptr;
 
     MultiArgs &ma = w->ma;
     ma.g = L->g;
@@ -232,6 +239,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     ma.spts = spts;
     ma.res_id = res_id;
     ma.res_d = res_d;
+    ma.win = win;
     guard.w = nullptr;
     *out = w;
     return SJ_OK;
@@ -307,6 +315,8 @@ extern "C" sj_status sj_engine_round(sj_engine *E, const sj_request *reqs, int32
         if (r.layer->device != dev) return fail(SJ_ERR_INVALID, "layer belongs to another device");
         if (r.N < 0 || r.N > 2147483647LL) return fail(SJ_ERR_INVALID, "request N out of range");
         if (r.N > 0 && (!r.pts || !r.out_id || !aligned16(r.pts))) return fail(SJ_ERR_INVALID, "bad request buffers");
+        if (r.use_window && (r.layer->kind != KIND_P2P || !(r.window >= 0.0 && r.window <= r.layer->D)))
+            return fail(SJ_ERR_INVALID, "a request window needs a polyline layer and 0 <= window <= its D");
         if (E->form == SJ_FP32X && r.layer->xmax > 1e30)
             return fail(SJ_ERR_INVALID, "SJ_FP32X needs grid coordinates below 1e30 in magnitude");
         if (std::find(layers.begin(), layers.end(), r.layer) == layers.end()) layers.push_back(r.layer);
@@ -334,7 +344,7 @@ extern "C" sj_status sj_engine_round(sj_engine *E, const sj_request *reqs, int32
         const int sl = w->slot;
         w->slot ^= 1;
         CUDA_TRY(cudaEventSynchronize(w->copied[sl]));   // its previous copy has been consumed
-        int nr = 0, off = 0;
+        int nr = 0, off = 0, windows = 0;
         for (int k = 0; k < n; ++k) {
             const sj_request &r = reqs[k];
             if (r.layer != L || r.N == 0) continue;
@@ -342,6 +352,8 @@ extern "C" sj_status sj_engine_round(sj_engine *E, const sj_request *reqs, int32
             d.pts = (const double2 *)r.pts;
             d.out_id = r.out_id;
             d.out_d = L->kind == KIND_P2P ? r.out_d : nullptr;
+            d.window = r.use_window ? r.window : L->D;
+            if (d.window < L->D) windows = 1;
             d.off = off;
             d.n = (int)r.N;
             w->h_reqs[sl][nr++] = d;
@@ -352,6 +364,7 @@ extern "C" sj_status sj_engine_round(sj_engine *E, const sj_request *reqs, int32
         if (nr == 0) continue;
         w->h_meta[sl][0] = nr;
         w->h_meta[sl][1] = off;
+        w->h_meta[sl][2] = windows;
         CUDA_TRY(cudaMemcpyAsync(w->d_reqs, w->h_reqs[sl], sizeof(ReqDev) * (size_t)nr, cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaMemcpyAsync(w->d_meta, w->h_meta[sl], sizeof(int) * 4, cudaMemcpyHostToDevice, s));
         CUDA_TRY(cudaEventRecord(w->copied[sl], s));

@@ -207,6 +207,11 @@ struct RefineArgs {
     double D;                // P2P window
     float Ddn, Dup;          // FP32 D rounded down / up with a 1e-12 relative margin
     float Df;                // D rounded to FP32 (staging prune)
+    // per-point windows (batched rounds whose requests ask for windows below
+    // D): when win_on and *win_on != 0, point slot j is joined within win[j]
+    // (<= D) instead of D; the lists and the staging prune stay those of D
+    const double *win;
+    const int *win_on;
     float eps_abs;           // absolute term of the split-coordinate rounding bound
     const float *frame_x;    // [nx] FP32 cell frame origins along x
     const float *frame_y;    // [ny]

@@ -149,6 +149,13 @@ __device__ __forceinline__ Best<T> shfl_best(const Best<T> &s, int o) {
     return r;
 }
 
+// A window w in FP32, rounded down / up with the same 1e-12 relative margin
+// the layer's D gets on the host (explicit roundings, no contraction).
+__device__ __forceinline__ void window_f32(double w, float &dn, float &up) {
+    dn = __double2float_rd(__dmul_rn(w, 1.0 - 1e-12));
+    up = __double2float_ru(__dadd_rn(__dmul_rn(w, 1.0 + 1e-12), 1e-300));
+}
+
 __device__ __forceinline__ float warp_min(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
@@ -199,7 +206,9 @@ __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, in
     }
 }
 
-template <bool FP32>
+// PW: per-point windows (a.win_on set; batched rounds).  The direct joins use
+// PW = false, whose code has no window load at all.
+template <bool FP32, bool PW>
 __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
     using T = typename std::conditional<FP32, float, double>::type;
     constexpr int SMAX = P2PSmem<FP32>::SMAX;
@@ -212,6 +221,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
     const unsigned lt_mask = (1u << lane) - 1u;
     unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0;
     unsigned c_fb = 0, c_hits = 0;
+    const bool pw = PW && *a.win_on;   // per-point windows in this launch (uniform)
 
     // Items come from a device counter when a.work_next is set (the next index
     // is fetched at the start of an item, so its latency hides behind the
@@ -336,8 +346,10 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                     const float2 p = s.pt[q];
                     const float e = fmaf(64.0f * U32, fmaxf(mag, fmaxf(fabsf(p.x), fabsf(p.y))), 4.0f * a.eps_abs) *
                                     (1.0f + 8.0f * U32);
-                    if (!((d - e) * (1.0f - 4.0f * U32) > a.Dup)) {                  // not certainly outside D
-                        const bool in_window = (d + e) * (1.0f + 4.0f * U32) < a.Ddn;
+                    float Ddn = a.Ddn, Dup = a.Dup;
+                    if (pw) window_f32(a.win[j0 + q], Ddn, Dup);
+                    if (!((d - e) * (1.0f - 4.0f * U32) > Dup)) {                    // not certainly outside D
+                        const bool in_window = (d + e) * (1.0f + 4.0f * U32) < Ddn;
                         const bool separated = (d2 - d) * (1.0f - 4.0f * U32) > 2.0f * e * (1.0f + 4.0f * U32);
                         if (!(in_window && separated)) {                              // redo in FP64
                             const int slot = atomicAdd(a.n_fb, 1);
@@ -351,7 +363,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
                     }
                 } else {
                     const double d = sqrt(s.b1[q]);
-                    if (d <= a.D) {
+                    if (d <= (pw ? a.win[j0 + q] : a.D)) {
                         out = id;
                         dd = d;
                     }
@@ -400,6 +412,7 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     const int n = *a.n_fb;
     const double INF = __longlong_as_double(0x7ff0000000000000LL);
+    const bool pw = a.win_on && *a.win_on;
     unsigned c_hits = 0;
     for (int f = warp; f < n; f += nwarps) {
         const int2 e = a.fb[f];
@@ -413,7 +426,7 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
         }
         for (int o = 16; o > 0; o >>= 1) st = merge<false>(st, shfl_best<false>(st, o));
         const double best = sqrt(st.b1);
-        const bool hit = st.i1 >= 0 && best <= a.D;
+        const bool hit = st.i1 >= 0 && best <= (pw ? a.win[j] : a.D);
         if (lane == 0) {
             if (a.res_id) {
                 a.res_id[j] = hit ? st.i1 : -1;
@@ -437,11 +450,11 @@ static size_t p2p_smem_bytes() {
     return sizeof(P2PSmem<FP32>) * P2P_WARPS;
 }
 
-template <bool FP32>
+template <bool FP32, bool PW>
 static cudaError_t p2p_prepare() {
     static bool done = false;   // per process; the attribute is per function
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2p_refine<FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_p2p_refine<FP32, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)p2p_smem_bytes<FP32>());
         if (e != cudaSuccess) return e;
         done = true;
@@ -449,17 +462,19 @@ static cudaError_t p2p_prepare() {
     return cudaSuccess;
 }
 
+template <bool FP32, bool PW>
+static cudaError_t p2p_launch(const RefineArgs &a, int blocks, cudaStream_t s) {
+    cudaError_t e = p2p_prepare<FP32, PW>();
+    if (e != cudaSuccess) return e;
+    k_p2p_refine<FP32, PW><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<FP32>(), s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_p2p_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
     (void)warps_per_block;
-    cudaError_t e;
-    if (form == SJ_FP32X) {
-        if ((e = p2p_prepare<true>()) != cudaSuccess) return e;
-        k_p2p_refine<true><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<true>(), s>>>(a);
-    } else {
-        if ((e = p2p_prepare<false>()) != cudaSuccess) return e;
-        k_p2p_refine<false><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<false>(), s>>>(a);
-    }
-    return cudaGetLastError();
+    const bool pw = a.win && a.win_on;
+    if (form == SJ_FP32X) return pw ? p2p_launch<true, true>(a, blocks, s) : p2p_launch<true, false>(a, blocks, s);
+    return pw ? p2p_launch<false, true>(a, blocks, s) : p2p_launch<false, false>(a, blocks, s);
 }
 
 cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s) {
@@ -470,11 +485,12 @@ cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s) 
 int p2p_blocks_per_sm(int form) {
     int n = 0;
     if (form == SJ_FP32X) {
-        if (p2p_prepare<true>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true>, P2P_WARPS * 32, p2p_smem_bytes<true>());
+        if (p2p_prepare<true, false>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true, false>, P2P_WARPS * 32,
+                                                      p2p_smem_bytes<true>());
     } else {
-        if (p2p_prepare<false>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false>, P2P_WARPS * 32,
+        if (p2p_prepare<false, false>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false, false>, P2P_WARPS * 32,
                                                       p2p_smem_bytes<false>());
     }
     return n > 0 ? n : 1;

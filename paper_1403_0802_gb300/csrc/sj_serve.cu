@@ -280,6 +280,8 @@ bool sj_server::launch_round() {
             t[k].N = q->r.n;
             t[k].out_id = q->d_id;
             t[k].out_d = q->d_d;
+            t[k].use_window = q->r.use_window;
+            t[k].window = q->r.window;
         }
         st = sj_engine_round(engine, t.data(), (int32_t)t.size(), compute);
     } else {
@@ -288,8 +290,12 @@ bool sj_server::launch_round() {
         o.launch = SJ_PER_REQUEST;
         o.pts_per_item = ppi;
         for (Req *q : rd.reqs) {
-            st = q->r.kind == SJ_SERVE_PIP ? sj_pip_join(layers[0], q->d_pts, q->r.n, q->d_id, &o, compute)
-                                           : sj_p2p_join(layers[1], q->d_pts, q->r.n, q->d_id, q->d_d, &o, compute);
+            if (q->r.kind == SJ_SERVE_PIP)
+                st = sj_pip_join(layers[0], q->d_pts, q->r.n, q->d_id, &o, compute);
+            else if (q->r.use_window)
+                st = sj_p2p_join_window(layers[1], q->d_pts, q->r.n, q->r.window, q->d_id, q->d_d, &o, compute);
+            else
+                st = sj_p2p_join(layers[1], q->d_pts, q->r.n, q->d_id, q->d_d, &o, compute);
             if (st != SJ_OK) break;
         }
     }
@@ -493,6 +499,8 @@ extern "C" sj_status sj_server_submit(sj_server *S, const sj_serve_request *req,
     if (!S->layers[r.kind]) return fail(SJ_ERR_INVALID, "the server has no layer of this kind");
     if (r.n < 1 || r.n > S->round_points) return fail(SJ_ERR_INVALID, "request size out of range");
     if (!r.pts || !r.out_id) return fail(SJ_ERR_INVALID, "NULL buffer");
+    if (r.use_window && (r.kind != SJ_SERVE_P2P || !(r.window >= 0.0 && r.window <= S->layers[r.kind]->D)))
+        return fail(SJ_ERR_INVALID, "a request window needs a P2P request and 0 <= window <= the layer's D");
     if (request_bytes(r) > S->ring.cap) return fail(SJ_ERR_INVALID, "request larger than the device budget");
     Req *q = new Req();
     q->r = r;

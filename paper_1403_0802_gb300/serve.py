@@ -40,6 +40,7 @@ class Request:
     t_done: float = math.nan
     out_id: torch.Tensor | None = None    # pinned host int32 [N]
     out_d: torch.Tensor | None = None     # pinned host float64 [N] (P2P)
+    window: float | None = None           # P2P: window of this request (None = the layer's D)
 
     @property
     def n(self) -> int:
@@ -52,10 +53,11 @@ class Request:
 
 def make_stream(n_requests: int, rate_per_s: float, pool_pip: torch.Tensor, pool_p2p: torch.Tensor,
                 size_min: int = 1_000, size_max: int = 5_000_000, pip_frac: float = 0.7,
-                seed: int = 20140309) -> list[Request]:
+                seed: int = 20140309, p2p_windows: tuple[float, ...] | None = None) -> list[Request]:
     """Poisson arrivals (all at t = 0 when rate_per_s is 0); sizes log-uniform in
     [size_min, size_max]; points are slices of pinned host pools of clustered
-    points (one pool per kind)."""
+    points (one pool per kind); each P2P request asks for a window drawn
+    uniformly from p2p_windows (None: the layer's D)."""
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate_per_s, n_requests)) if rate_per_s > 0 else np.zeros(n_requests)
     reqs = []
@@ -65,7 +67,8 @@ def make_stream(n_requests: int, rate_per_s: float, pool_pip: torch.Tensor, pool
         n = int(round(math.exp(rng.uniform(math.log(size_min), math.log(size_max)))))
         n = min(n, pool.shape[0])
         off = int(rng.integers(0, pool.shape[0] - n + 1))
-        reqs.append(Request(k, float(t[k]), kind, pool[off:off + n]))
+        win = float(p2p_windows[int(rng.integers(0, len(p2p_windows)))]) if (p2p_windows and kind == P2P) else None
+        reqs.append(Request(k, float(t[k]), kind, pool[off:off + n], window=win))
     return reqs
 
 
@@ -126,6 +129,8 @@ class Server:
             req.out_id = r.out_id.data_ptr()
             req.out_d = r.out_d.data_ptr() if r.out_d is not None else None
             req.not_before = t0 + r.arrival
+            req.use_window = 0 if r.window is None else 1
+            req.window = 0.0 if r.window is None else r.window
             L.check(lib.sj_server_submit(self.handle, C.byref(req), C.byref(tk)), "sj_server_submit")
             tickets.append(tk.value)
         late = max(lib.sj_server_now(self.handle) - t0 - order[-1].arrival, 0.0)   # submission behind schedule

@@ -62,6 +62,10 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(libsj):
     assert b"grid" in lib.sj_last_error()
     st = lib.sj_bucket_points(None, 0, C.byref(bad), None, None, None)
     assert st == _lib.SJ_ERR_INVALID
+    for w in (-1.0, float("nan")):    # a per-call P2P window is checked before the layer is touched
+        st = lib.sj_p2p_join_window(None, None, 0, w, None, None, None, None)
+        assert st == _lib.SJ_ERR_INVALID
+        assert b"window" in lib.sj_last_error()
 
 
 def test_struct_layouts_match_header():
@@ -81,17 +85,43 @@ def test_binding_imports_without_a_gpu():
     assert (o.form, o.launch, o.pts_per_item, o.flags) == (1, 1, 32, 1)
 
 
-def test_request_struct_layout():
+C_STRUCTS = ("sj_grid", "sj_opts", "sj_layer_info", "sj_run_stats", "sj_peak_rates", "sj_request",
+             "sj_serve_request", "sj_server_stats")
+
+
+def test_struct_layouts_match_the_c_compiler(tmp_path):
+    """Every struct the binding declares has the size and field offsets that
+    the host C compiler gives the header's struct."""
+    import shutil
+    import subprocess
     from paper_1403_0802_gb300 import _lib
-    assert C.sizeof(_lib.sj_request) == 40
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sj.h"', '#include "sj_serve.h"', '#include "sj_peaks.h"',
+             "int main(void) {"]
+    for name in C_STRUCTS:
+        lines.append(f'printf("{name} %zu\\n", sizeof({name}));')
+        for f, _ in getattr(_lib, name)._fields_:
+            lines.append(f'printf("{name}.{f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", INCLUDE, str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                  text=True).stdout.splitlines())
+    for name in C_STRUCTS:
+        T = getattr(_lib, name)
+        assert int(got[name]) == C.sizeof(T), name
+        for f, _ in T._fields_:
+            assert int(got[f"{name}.{f}"]) == getattr(T, f).offset, (name, f)
 
 
 def test_server_struct_layouts_and_argument_checks(libsj):
     """include/sj_serve.h: struct sizes, and argument errors reported without
     touching a GPU."""
     from paper_1403_0802_gb300 import _lib
-    assert C.sizeof(_lib.sj_serve_request) == 48
-    assert C.sizeof(_lib.sj_server_stats) == 48
     lib = _lib.lib()
     h = C.c_void_p()
     assert lib.sj_server_create(None, None, None, 0, 1 << 20, 1000, 8, C.byref(h)) == _lib.SJ_ERR_INVALID

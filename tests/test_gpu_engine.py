@@ -75,6 +75,47 @@ def test_rounds_match_single_joins(setup, form, graph):
                         assert np.all(np.isinf(a_d[a_id < 0]))
 
 
+@pytest.mark.parametrize("form", ["fp64", "fp32x"])
+def test_rounds_with_per_request_windows(setup, form):
+    """P2P requests of one round ask for different windows (none, 0, 20 m,
+    60 m, the layer's D): each equals sj_p2p_join_window at its window alone.
+    Rounds alternate between windowed and unwindowed, so one captured graph
+    serves both."""
+    api, pip, p2p, ptsP, ptsL = setup
+    D = p2p.D
+    rng = np.random.default_rng(8)
+    stream = torch.cuda.Stream()
+    wins = [None, 0.0, 20.0, 60.0, D]
+    with api.Engine(max_points=600_000, max_requests=64, form=form) as eng:
+        for rnd in range(4):
+            reqs = []
+            for k in range(8):
+                size = int(rng.choice([1, 999, 30_000]))
+                off = int(rng.integers(0, ptsL.shape[0] - size))
+                win = wins[(k + rnd) % len(wins)] if rnd % 2 == 0 else None
+                reqs.append((p2p, ptsL[off:off + size].contiguous(),
+                             torch.full((size,), 99, dtype=torch.int32, device="cuda"),
+                             torch.full((size,), -5.0, dtype=torch.float64, device="cuda"), win))
+            stream.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(stream):
+                eng.round(reqs, stream)
+            stream.synchronize()
+            for layer, pts, out_id, out_d, win in reqs:
+                rid, rd = api.p2p_join(layer, pts, form=form, window=win)
+                torch.cuda.synchronize()
+                a_id, a_d, b_id, b_d = (t.cpu().numpy() for t in (out_id, out_d, rid, rd))
+                if form == "fp64":
+                    np.testing.assert_array_equal(a_id, b_id)
+                    np.testing.assert_array_equal(a_d, b_d)
+                else:
+                    assert (a_id == b_id).mean() > 0.999, (rnd, win, pts.shape)
+                    both = (a_id >= 0) & (a_id == b_id)
+                    assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
+                    assert np.all(np.isinf(a_d[a_id < 0]))
+                if win is not None:
+                    assert np.all(a_d[a_id >= 0] <= win)
+
+
 def test_round_limits(setup):
     api, pip, p2p, ptsP, ptsL = setup
     from paper_1403_0802_gb300._lib import SJError, SJ_ERR_INVALID
@@ -87,3 +128,9 @@ def test_round_limits(setup):
         outs = [torch.empty(10, dtype=torch.int32, device="cuda") for _ in range(3)]
         with pytest.raises(SJError):
             eng.round([(pip, small, o, None) for o in outs])         # 3 requests > max_requests
+        ls = ptsL[:10].contiguous()
+        oi, od = outs[0], torch.empty(10, dtype=torch.float64, device="cuda")
+        for bad in ((pip, small, oi, None, 5.0), (p2p, ls, oi, od, -1.0), (p2p, ls, oi, od, 1e9)):
+            with pytest.raises(SJError) as e:
+                eng.round([bad])                                    # windows: P2P only, within [0, D]
+            assert e.value.status == SJ_ERR_INVALID

@@ -64,7 +64,7 @@ def fp32x_bound(oracle, g, pts, mbb, cs, ci):
     return 64.0 * 2.0 ** -24 * m * 1.0001 + 1e-9
 
 
-def check_p2p(oracle, w, gid, gd, form, verts=None, line_off=None):
+def check_p2p(oracle, w, gid, gd, form, verts=None, line_off=None, D_layer=None):
     L = w.polylines if verts is None else None
     verts = L.verts if verts is None else verts
     line_off = L.line_off if line_off is None else line_off
@@ -81,7 +81,7 @@ def check_p2p(oracle, w, gid, gd, form, verts=None, line_off=None):
         lim = 1e-12 * np.maximum(rd[both], 1.0)
     else:
         mbb = oracle.p2p_mbb(w.grid, verts, line_off)
-        cs, ci = oracle.cand_csr(w.grid, mbb, w.D, expand=True)
+        cs, ci = oracle.cand_csr(w.grid, mbb, w.D if D_layer is None else D_layer, expand=True)
         lim = fp32x_bound(oracle, w.grid, w.points, mbb, cs, ci)[both]
     worst = np.flatnonzero(err > lim)
     assert worst.size == 0, (form, err[worst[:5]], lim[worst[:5]])
@@ -383,6 +383,66 @@ def test_p2p_window_larger_than_the_extent(api, oracle, form):
     r = check_p2p(oracle, w, to_np(gid), to_np(gd), form)
     inside = (pts[:, 0] >= 0) & (pts[:, 0] < 2048) & (pts[:, 1] >= 0) & (pts[:, 1] < 2048)
     assert (to_np(gid)[inside] >= 0).all() and (to_np(gid)[~inside] < 0).all()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_p2p_window_per_call(api, oracle, form):
+    """One resident layer built for D = 100 m answers windows 0, 10, 37.5 and
+    100 m per call (sj_p2p_join_window); each equals the oracle's join at that
+    window, and the window D equals sj_p2p_join bit for bit."""
+    w = synth.p2p_walks(n_points=200_003, n_lines=20_000)
+    Lw = w.polylines
+    D = w.D
+    with api.p2p_layer(Lw.verts, Lw.line_off, D, w.grid) as layer:
+        pts = torch.as_tensor(w.points, device="cuda")
+        fid, fd = api.p2p_join(layer, pts, form=form)
+        hits = []
+        for win in (0.0, 10.0, 37.5, D):
+            gid, gd = api.p2p_join(layer, pts, form=form, window=win)
+            w.D = win
+            r = check_p2p(oracle, w, to_np(gid), to_np(gd), form, D_layer=D)
+            hits.append(r["hit_frac"])
+            if win == D:
+                assert torch.equal(gid, fid) and torch.equal(gd, fd)
+        w.D = D
+        for bad in (-1.0, D * (1 + 1e-9), float("nan")):
+            with pytest.raises(Exception) as e:
+                api.p2p_join(layer, pts, form=form, window=bad)
+            assert "window" in str(e.value)
+    assert hits[0] < hits[1] < hits[2] < hits[3]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("win", [25.0, 50.0])
+def test_p2p_window_per_call_at_cell_boundaries(api, oracle, form, win):
+    """Windows smaller than the layer's D = 100 m on the axis-aligned 25 m
+    lattice, points just inside and just outside the window: the layer's
+    lists, built for D, must give exactly the window's answers."""
+    rng = np.random.default_rng(int(win) + 5)
+    g = dict(x0=0.0, y0=0.0, x1=6400.0, y1=6400.0, nx=64, ny=64)
+    lines = []
+    for _ in range(400):
+        x, y = 25.0 * rng.integers(8, 248, 2)
+        k = int(rng.integers(1, 5))
+        lines.append([(x, y), (x + 25.0 * k, y)] if rng.random() < 0.5 else [(x, y), (x, y + 25.0 * k)])
+    verts = np.concatenate([np.asarray(l, np.float64) for l in lines])
+    off = np.arange(0, 2 * len(lines) + 1, 2, dtype=np.int64)
+    pts = []
+    for s_ in (1.0 - 1e-7, 1.0 + 1e-7):
+        r = win * s_
+        for (ax, ay), (bx, by) in lines:
+            for (px, py) in ((ax, ay), (bx, by), (0.5 * (ax + bx), 0.5 * (ay + by))):
+                for (ux, uy) in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+                    pts.append((px + r * ux, py + r * uy))
+    pts = np.asarray(pts, np.float64)
+
+    class W:
+        pass
+    w = W()
+    w.grid, w.points, w.D, w.polylines = g, pts, win, None
+    with api.p2p_layer(verts, off, 100.0, g) as layer:
+        gid, gd = api.p2p_join(layer, pts, form=form, window=win)
+    check_p2p(oracle, w, to_np(gid), to_np(gd), form, verts=verts, line_off=off, D_layer=100.0)
 
 
 @pytest.mark.parametrize("form", FORMS)

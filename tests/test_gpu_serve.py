@@ -60,6 +60,30 @@ def test_mix_equals_alone(server, mode, form):
             assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
 
 
+@pytest.mark.parametrize("mode", ["batched", "per_request"])
+def test_per_request_windows(server, mode):
+    """P2P requests with their own windows (below the layer's D) share rounds
+    with unwindowed ones; each equals sj_p2p_join_window at its window."""
+    api, serve, srv, pool_p, pool_l = server
+    reqs = serve.make_stream(60, rate_per_s=200_000.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=100,
+                             size_max=60_000, seed=9, pip_frac=0.3, p2p_windows=(0.0, 10.0, 40.0, 100.0))
+    assert len({r.window for r in reqs if r.kind == serve.P2P}) > 2
+    srv.run(reqs, mode=mode)
+    for r in reqs:
+        layer = srv.layers[r.kind]
+        pts = r.pts.cuda()
+        if r.kind == serve.PIP:
+            assert torch.equal(r.out_id, api.pip_join(layer, pts, form=srv.form).cpu()), r.rid
+            continue
+        rid, rd = api.p2p_join(layer, pts, form=srv.form, window=r.window)
+        a_id, a_d = r.out_id.numpy(), r.out_d.numpy()
+        b_id, b_d = rid.cpu().numpy(), rd.cpu().numpy()
+        assert (a_id == b_id).mean() > 0.999, (r.rid, r.window)
+        both = (a_id >= 0) & (a_id == b_id)
+        assert np.all(np.abs(a_d[both] - b_d[both]) <= 1e-2)
+        assert np.all(a_d[a_id >= 0] <= r.window)
+
+
 def test_arrivals_are_not_admitted_early(server):
     """A request submitted with a future arrival time is not served before it
     (its latency is measured from that arrival)."""
