@@ -5,7 +5,8 @@ Workloads (--workload):
          polylines (2-40 vertices), window D = 100 m, grid 512 x 512
   pip    PIP, 1,000,000 uniform points, 1,024 star polygons, grid 256 x 256
   pip3   PIP at scale, 100,000,000 clustered points against the 40,000-tile
-         layer (--layer 1) or the 14,000-tile heavy-tail layer (--layer 2)
+         layer (--layer 1), the 14,000-tile heavy-tail layer (--layer 2) or the
+         multi-ring layer (--layer 3: layer 1 with island holes, ~70,000 polygons)
   p2p4   P2P at scale, 170,000,000 clustered points, 150,000 lognormal walks,
          D = --D (50, 100 or 200 m)
   serve  continuous batching: a Poisson stream of GPS batches (1k-5M points,
@@ -52,7 +53,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["p2p", "pip", "pip3", "p2p4", "serve"], default="p2p")
-    ap.add_argument("--layer", type=int, default=1, help="pip3: tiling layer 1 or 2")
+    ap.add_argument("--layer", type=int, default=1, choices=[1, 2, 3],
+                    help="pip3: tiling layer 1, 2 or 3 (multi-ring)")
     ap.add_argument("--D", type=float, default=100.0, help="p2p4: window")
     ap.add_argument("--points", type=int, default=0, help="override the workload's point count")
     ap.add_argument("--form", choices=["fp32x", "fp64"], default="fp32x")

@@ -58,6 +58,8 @@ def _load():
         sig = {
             "or_set_threads": (None, [C.c_int]),
             "or_max_threads": (C.c_int, []),
+            "or_set_exact": (None, [C.c_int]),
+            "or_cross_sign": (C.c_int, [d, d, d, d, d, d]),
             "or_point_cell": (i64, [gp, d, d]),
             "or_point_cells": (None, [gp, p, i64, p]),
             "or_cell_counts": (C.c_int, [gp, p, i64, p]),
@@ -114,6 +116,24 @@ def set_threads(n: int | None = None) -> int:
     n = lib.or_max_threads() if n is None else int(n)
     lib.or_set_threads(n)
     return n
+
+
+class exact_predicates:
+    """Context manager: PIP crossing signs from the exact value of the
+    determinant (Shewchuk's adaptive predicate) instead of its FP64 value."""
+
+    def __enter__(self):
+        _load().or_set_exact(1)
+        return self
+
+    def __exit__(self, *exc):
+        _load().or_set_exact(0)
+
+
+def cross_sign(hx, hy, lx, ly, px, py) -> int:
+    """Sign (-1, 0, 1) the crossing rule takes for
+    (hx - lx)(py - ly) - (hy - ly)(px - lx) in the current mode."""
+    return int(_load().or_cross_sign(float(hx), float(hy), float(lx), float(ly), float(px), float(py)))
 
 
 def point_cell(g, x: float, y: float) -> int:

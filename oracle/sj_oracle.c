@@ -26,6 +26,10 @@
  *     with lo = the endpoint whose y <= p.y and hi = the other,
  *     d = (hi.x - lo.x) * (p.y - lo.y) - (hi.y - lo.y) * (p.x - lo.x) and the
  *     edge counts iff d > 0.  Inside iff the count over all rings is odd.
+ *     d's sign is taken from its FP64 evaluation (the default, the method's
+ *     arithmetic) or, in the exact-predicate mode (or_set_exact(1)), from the
+ *     exact value of d for the given doubles (Shewchuk's adaptive orientation
+ *     predicate: an FP64 filter, then error-free expansion arithmetic).
  *   - a point inside several polygons gets the smallest id.
  *   - P2P window is inclusive (d <= R); exact distance ties go to the smaller id.
  *   - the P2P cell range uses lo = nextafter(xmin - R, -inf),
@@ -216,6 +220,89 @@ int or_cand_csr(const or_grid *g, const double *mbb, int32_t nobj, double R, int
 
 /* ------------------------------------------------------------------ PIP (Sec. III.C) */
 
+/* Exact sign of the crossing determinant, after J. R. Shewchuk, "Adaptive
+ * Precision Floating-Point Arithmetic and Fast Robust Geometric Predicates"
+ * (Discrete Comput. Geom. 18, 1997).  An expansion is a list of doubles,
+ * nonoverlapping and ordered by increasing magnitude, whose exact sum is the
+ * value it stands for; its sign is the sign of its largest nonzero
+ * component.  Inputs are assumed far from overflow and underflow (true for
+ * coordinates of a bounded grid). */
+static int g_exact = 0;
+void or_set_exact(int on) { g_exact = on ? 1 : 0; }
+
+/* s + t = a + b exactly, s = fl(a + b) (Knuth's two-sum, Shewchuk Thm. 7). */
+static void two_sum(double a, double b, double *s, double *t) {
+    double x = a + b;
+    double bv = x - a;
+    double av = x - bv;
+    *s = x;
+    *t = (a - av) + (b - bv);
+}
+
+/* p + t = a * b exactly, p = fl(a * b): the fused multiply-add rounds once,
+ * so a * b - p is exact. */
+static void two_prod(double a, double b, double *p, double *t) {
+    double x = a * b;
+    *p = x;
+    *t = fma(a, b, -x);
+}
+
+/* Add the double b to the expansion h[0..m) in place (Shewchuk's
+ * Grow-Expansion, Thm. 10); returns the new length m + 1. */
+static int grow(double *h, int m, double b) {
+    double q = b;
+    for (int i = 0; i < m; ++i) {
+        double s, t;
+        two_sum(q, h[i], &s, &t);
+        h[i] = t;
+        q = s;
+    }
+    h[m] = q;
+    return m + 1;
+}
+
+/* Exact sign of (hx - lx) * (py - ly) - (hy - ly) * (px - lx). */
+static int cross_sign_exact(double hx, double hy, double lx, double ly, double px, double py) {
+    double dl = (hx - lx) * (py - ly), dr = (hy - ly) * (px - lx);
+    double d = dl - dr;
+    /* filter: the FP64 value's error is below (3 eps + 16 eps^2)(|dl| + |dr|),
+     * eps = 2^-53 (Shewchuk's bound for this orientation form) */
+    const double eps = 1.1102230246251565e-16;
+    double bound = (3.0 * eps + 16.0 * eps * eps) * (fabs(dl) + fabs(dr));
+    if (d > bound) return 1;
+    if (-d > bound) return -1;
+    /* each difference as an exact two-term sum, each product of two such sums
+     * as four exact two-term products: sixteen doubles summing to d exactly */
+    double a[2], b[2], c[2], e[2];
+    two_sum(hx, -lx, &a[1], &a[0]);
+    two_sum(py, -ly, &b[1], &b[0]);
+    two_sum(hy, -ly, &c[1], &c[0]);
+    two_sum(px, -lx, &e[1], &e[0]);
+    double h[16];
+    int m = 0;
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+            double p, t;
+            two_prod(a[i], b[j], &p, &t);
+            m = grow(h, m, t);
+            m = grow(h, m, p);
+            two_prod(c[i], e[j], &p, &t);
+            m = grow(h, m, -t);
+            m = grow(h, m, -p);
+        }
+    for (int i = m - 1; i >= 0; --i)
+        if (h[i] != 0.0) return h[i] > 0.0 ? 1 : -1;
+    return 0;
+}
+
+/* Exported for tests: the sign the crossing rule takes for d (-1, 0, 1) in the
+ * current mode. */
+int or_cross_sign(double hx, double hy, double lx, double ly, double px, double py) {
+    if (g_exact) return cross_sign_exact(hx, hy, lx, ly, px, py);
+    double d = (hx - lx) * (py - ly) - (hy - ly) * (px - lx);
+    return (d > 0.0) - (d < 0.0);
+}
+
 /* Crossing parity of point p against ring [b, e) (implicitly closed). */
 static int ring_parity(double px, double py, const double *v, int64_t b, int64_t e) {
     int odd = 0;
@@ -229,8 +316,12 @@ static int ring_parity(double px, double py, const double *v, int64_t b, int64_t
         double lx, ly, hx, hy;
         if (a_above) { hx = ax; hy = ay; lx = bx; ly = by; }
         else         { lx = ax; ly = ay; hx = bx; hy = by; }
-        double d = (hx - lx) * (py - ly) - (hy - ly) * (px - lx);
-        if (d > 0.0) odd ^= 1;
+        if (g_exact) {
+            if (cross_sign_exact(hx, hy, lx, ly, px, py) > 0) odd ^= 1;
+        } else {
+            double d = (hx - lx) * (py - ly) - (hy - ly) * (px - lx);
+            if (d > 0.0) odd ^= 1;
+        }
     }
     return odd;
 }

@@ -204,6 +204,59 @@ def tiling(rng: np.random.Generator, nx: int, ny: int, side_median: float, side_
     return PolygonLayer(v, ring_off, np.arange(len(sizes) + 1, dtype=np.int64))
 
 
+def with_islands(rng: np.random.Generator, tiles: PolygonLayer, nx: int, ny: int, hole_frac: float = 0.3,
+                 max_holes: int = 4, hole_median: float = 12.0, hole_sigma: float = 0.8, hole_cap: int = 400,
+                 extent: float = EXTENT) -> PolygonLayer:
+    """Multi-ring version of an nx x ny tiling (WWF-like enclaves): a fraction
+    hole_frac of the tiles get 1..max_holes holes, and each hole is also the
+    single ring of a new "island" polygon, so the layer still tiles the extent
+    without gaps or overlaps.  Holes are star-shaped (sorted angles, largest gap
+    below pi) with k = clamp(round(lognormal(ln hole_median, hole_sigma)), 4,
+    hole_cap) vertices, one per quarter of the tile's lattice cell, centred at
+    (0.375 or 0.625) +- 0.02 cells with radius U(0.05, 0.10) cells: inside
+    [0.25, 0.75]^2 of the cell, which the jittered and bulged tile sides
+    (at most 0.2 cells from the lattice lines) never reach, and disjoint.
+    Polygon ids: tiles keep row * nx + col; islands follow in tile order."""
+    cw, ch = extent / nx, extent / ny
+    n_tiles = tiles.n_polygons
+    verts = [tiles.verts]
+    ring_sizes = [tiles.ring_sizes()]
+    tile_rings = np.ones(n_tiles, np.int64)        # rings per tile polygon (outer + holes)
+    holes = []                                      # (tile, ring vertices) in tile order
+    quarters = np.array([(0.375, 0.375), (0.625, 0.375), (0.375, 0.625), (0.625, 0.625)])
+    chosen = np.flatnonzero(rng.random(n_tiles) < hole_frac)
+    for t in chosen:
+        col, row = t % nx, t // nx
+        nh = int(rng.integers(1, max_holes + 1))
+        for q in rng.permutation(4)[:nh]:
+            cx = (col + quarters[q, 0] + rng.uniform(-0.02, 0.02)) * cw
+            cy = (row + quarters[q, 1] + rng.uniform(-0.02, 0.02)) * ch
+            k = int(min(hole_cap, max(4, round(rng.lognormal(math.log(hole_median), hole_sigma)))))
+            ang = _sorted_angles(k, rng)
+            r = rng.uniform(0.05, 0.10, size=k)
+            holes.append((int(t), np.stack([cx + r * cw * np.cos(ang), cy + r * ch * np.sin(ang)], 1)))
+        tile_rings[t] += nh
+    # rings in polygon order: each tile's outer ring then its holes, then the islands
+    by_tile: dict[int, list[np.ndarray]] = {}
+    for t, h in holes:
+        by_tile.setdefault(t, []).append(h)
+    rings = []
+    off = tiles.ring_off
+    for t in range(n_tiles):
+        rings.append(tiles.verts[off[t]:off[t + 1]])
+        rings.extend(by_tile.get(t, ()))
+    island_rings = [h for t in sorted(by_tile) for h in by_tile[t]]
+    rings.extend(island_rings)
+    sizes = np.array([len(r) for r in rings], np.int64)
+    ring_off = np.zeros(len(rings) + 1, np.int64)
+    ring_off[1:] = np.cumsum(sizes)
+    rings_per_poly = np.concatenate([tile_rings, np.ones(len(island_rings), np.int64)])
+    poly_ring_off = np.zeros(len(rings_per_poly) + 1, np.int64)
+    poly_ring_off[1:] = np.cumsum(rings_per_poly)
+    del verts, ring_sizes
+    return PolygonLayer(np.ascontiguousarray(np.concatenate(rings)), ring_off, poly_ring_off)
+
+
 # --------------------------------------------------------------------------- polylines
 
 def _segmented_cumsum(vals: np.ndarray, starts: np.ndarray) -> np.ndarray:
@@ -306,12 +359,17 @@ def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE
     tiles (polygon median ~19, max ~5,000).  Layer 2: 140 x 100 tiles, side median
     90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000).  Filter
     grid 1024 x 1024 (the fastest of 512 / 1024 / 2048 per axis for both layers
-    at 100 M points on GB300)."""
+    at 100 M points on GB300).  Layer 3 (multi-ring, WWF-like): layer 1's
+    tiling with island holes in 30 % of the tiles (with_islands), about 70,000
+    polygons."""
     if grid_n is None:
         grid_n = 1024
     rng = np.random.default_rng(seed + 10 * layer)
     if layer == 1:
         P = tiling(rng, 200, 200, side_median=2.6, side_cap=1250, n_giant=3)
+    elif layer == 3:
+        P = with_islands(rng, tiling(np.random.default_rng(seed + 10), 200, 200, side_median=2.6, side_cap=1250,
+                                     n_giant=3), 200, 200)
     else:
         P = tiling(rng, 140, 100, side_median=90.0, side_cap=25000, n_giant=3)
     pts = points_mixture(n_points, _point_rng(np.random.default_rng(seed), seed, shard))

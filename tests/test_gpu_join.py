@@ -526,11 +526,12 @@ def test_cell_ids_exact_at_cell_boundaries(api, oracle, g):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("layer", [1, 2])
+@pytest.mark.parametrize("layer", [1, 2, 3])
 def test_pip_tiles_subset(api, oracle, form, layer):
     """PIP at scale on a 1,000,003-point subset: the clustered mixture against
-    the 40,000-tile layer (median 19, max 5,004 vertices) and the 14,000-tile
-    layer (median ~500, max 100,004 vertices, edges staged in many chunks)."""
+    the 40,000-tile layer (median 19, max 5,004 vertices), the 14,000-tile
+    layer (median ~500, max 100,004 vertices, edges staged in many chunks) and
+    the multi-ring layer (layer 1 with island holes and their islands)."""
     w = synth.pip_tiles(n_points=1_000_003, layer=layer)
     P = w.polygons
     ref, nh = oracle.pip_join(w.grid, w.points, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
@@ -548,12 +549,12 @@ def test_pip_tiles_subset(api, oracle, form, layer):
 SAMPLE = 200_000
 
 
-@pytest.mark.parametrize("layer", [1, 2])
+@pytest.mark.parametrize("layer", [1, 2, 3])
 def test_pip_at_scale_full_size_sampled(api, oracle, layer):
-    """100,000,000 clustered points against the 40,000-tile (layer 1) or the
-    heavy-tail 14,000-tile (layer 2) tiling, grid 1024 x 1024, FP32X: ids of
-    a 200,000-point sample bit-identical to the oracle; every point in exactly
-    one tile."""
+    """100,000,000 clustered points against the 40,000-tile (layer 1), the
+    heavy-tail 14,000-tile (layer 2) or the multi-ring (layer 3: layer 1 with
+    island holes) tiling, grid 1024 x 1024, FP32X: ids of a 200,000-point
+    sample bit-identical to the oracle; every point in exactly one polygon."""
     w = synth.pip_tiles(layer=layer)
     P = w.polygons
     with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer_:
@@ -565,6 +566,8 @@ def test_pip_at_scale_full_size_sampled(api, oracle, layer):
     idx = np.random.default_rng(layer).choice(len(w.points), SAMPLE, replace=False)
     ref = oracle.pip_join(w.grid, np.ascontiguousarray(w.points[idx]), P.verts, P.ring_off, P.poly_ring_off)
     np.testing.assert_array_equal(got[idx], ref)
+    if layer == 3:                                       # points in holes answer the island
+        assert (ref >= 40_000).sum() > 1000
 
 
 def test_p2p_at_scale_full_size_sampled(api, oracle):

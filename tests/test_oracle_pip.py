@@ -232,3 +232,111 @@ def test_synthetic_tiling_covers_every_point_once(oracle, side_median, cap):
     ids, nh = oracle.pip_join(g, pts, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
     np.testing.assert_array_equal(nh, 1)
     assert P.polygon_sizes().max() >= 4 * cap
+
+
+def test_islands_layer_covers_every_point_once(oracle):
+    """Holes of multi-ring tiles are also the rings of island polygons (the
+    WWF-like layer): every point lies in exactly one polygon, hole vertices
+    included; points in a hole take the island's id, not the tile's."""
+    rng = np.random.default_rng(23)
+    T = synth.tiling(rng, 12, 9, side_median=2.6, side_cap=50, extent=1000.0, n_giant=1)
+    P = synth.with_islands(rng, T, 12, 9, hole_frac=0.6, extent=1000.0)
+    n_tiles = 12 * 9
+    assert P.n_polygons > n_tiles and (np.diff(P.poly_ring_off)[:n_tiles] > 1).any()
+    g = synth.grid(32, extent=1000.0)
+    pts = np.concatenate([synth.points_uniform(40000, rng, extent=1000.0), P.verts[::5]])
+    pts = pts[(pts < 1000.0).all(1)]
+    ids, nh = oracle.pip_join(g, pts, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
+    np.testing.assert_array_equal(nh, 1)
+    assert (ids >= n_tiles).mean() > 0.005
+    # island i's ring is a hole of the tile whose lattice cell holds it
+    isl = np.flatnonzero(ids >= n_tiles)
+    cw, ch = 1000.0 / 12, 1000.0 / 9
+    for k in isl[:200]:
+        ring = P.ring_off[P.poly_ring_off[ids[k]]]
+        vx, vy = P.verts[ring]
+        t = int(vy // ch) * 12 + int(vx // cw)
+        r0, r1 = P.poly_ring_off[t], P.poly_ring_off[t + 1]
+        assert any(np.array_equal(P.verts[P.ring_off[r]:P.ring_off[r + 1]],
+                                  P.verts[ring:P.ring_off[P.poly_ring_off[ids[k]] + 1]]) for r in range(r0 + 1, r1))
+
+
+def _near_degenerate(rng, n):
+    """Points within a couple of ulps of the line through l and h, with l and h
+    of different magnitudes (so the FP64 differences round and the FP64 sign
+    is often zero or wrong)."""
+    l = rng.uniform(0.0, 1e5, (n, 2)) * rng.choice([1e-4, 1e-2, 1.0], (n, 1))
+    h = rng.uniform(0.0, 1e5, (n, 2))
+    t = rng.uniform(0.0, 1.0, n)
+    p = l + t[:, None] * (h - l)
+    k = rng.integers(-2, 3, n)
+    p[:, 0] = p[:, 0] + k * np.spacing(p[:, 0])
+    return l, h, p
+
+
+def test_exact_predicate_matches_rational_arithmetic(oracle):
+    """The exact mode's crossing sign equals the sign of the determinant in
+    exact rational arithmetic (Python fractions of the same doubles) on points
+    within a few ulps of the edge's line; the FP64 sign is wrong on some of
+    them (so the cases reach the expansion arithmetic)."""
+    from fractions import Fraction as F
+    rng = np.random.default_rng(31)
+    l, h, p = _near_degenerate(rng, 4000)
+    wrong64 = flipped64 = 0
+    with oracle.exact_predicates():
+        for i in range(len(p)):
+            hx, hy, lx, ly, px, py = (F(float(v)) for v in (h[i, 0], h[i, 1], l[i, 0], l[i, 1], p[i, 0], p[i, 1]))
+            d = (hx - lx) * (py - ly) - (hy - ly) * (px - lx)
+            want = (d > 0) - (d < 0)
+            got = oracle.cross_sign(h[i, 0], h[i, 1], l[i, 0], l[i, 1], p[i, 0], p[i, 1])
+            assert got == want, i
+    for i in range(len(p)):
+        hx, hy, lx, ly, px, py = (F(float(v)) for v in (h[i, 0], h[i, 1], l[i, 0], l[i, 1], p[i, 0], p[i, 1]))
+        d = (hx - lx) * (py - ly) - (hy - ly) * (px - lx)
+        f = oracle.cross_sign(h[i, 0], h[i, 1], l[i, 0], l[i, 1], p[i, 0], p[i, 1])
+        wrong64 += f != (d > 0) - (d < 0)
+        flipped64 += f * ((d > 0) - (d < 0)) < 0
+    assert wrong64 > 100 and flipped64 > 10          # zero and opposite FP64 signs both occur
+
+
+def test_exact_predicate_special_values(oracle):
+    """Closed forms: points exactly on an edge give 0; one ulp off gives the
+    side; exact arithmetic on integers far above 2^26 (where FP64 products
+    round) still decides."""
+    with oracle.exact_predicates():
+        assert oracle.cross_sign(3.0, 7.0, 0.0, 0.0, 1.5, 3.5) == 0
+        assert oracle.cross_sign(3.0, 7.0, 0.0, 0.0, np.nextafter(1.5, 0.0), 3.5) == 1
+        assert oracle.cross_sign(3.0, 7.0, 0.0, 0.0, np.nextafter(1.5, 9.0), 3.5) == -1
+        big = float(2 ** 40)
+        # l = (0, 0), h = (big + 1, big - 1), p = (big + 3, big - 1): d = -2 (big - 1) exactly
+        assert oracle.cross_sign(big + 1, big - 1, 0.0, 0.0, big + 3, big - 1) == -1
+        # collinear with integer coordinates beyond 2^53 / 2 products: d = 0
+        a = float(2 ** 30 + 3)
+        assert oracle.cross_sign(3 * a, 5 * a, 0.0, 0.0, 6 * a, 10 * a) == 0
+    assert oracle.cross_sign(3.0, 7.0, 0.0, 0.0, 1.5, 3.5) == 0      # FP64 mode is exact here too
+
+
+def test_exact_mode_tiling_and_workloads(oracle):
+    """Exact predicates keep the tiling invariant on points within ulps of the
+    shared edges, and agree with the FP64 rule on the synthetic workloads'
+    points (so ids equal to the FP64 oracle are also the exact answers)."""
+    rng = np.random.default_rng(41)
+    P = synth.with_islands(rng, synth.tiling(rng, 12, 9, side_median=8.0, side_cap=60, extent=1000.0), 12, 9,
+                           hole_frac=0.5, extent=1000.0)
+    g = synth.grid(32, extent=1000.0)
+    # points within a few ulps of edges: on the chord between consecutive vertices
+    v = P.verts
+    i = rng.integers(0, len(v) - 1, 20000)
+    t = rng.uniform(0.0, 1.0, len(i))
+    pe = v[i] + t[:, None] * (v[i + 1] - v[i])
+    pe = pe[(pe >= 0.0).all(1) & (pe < 1000.0).all(1)]
+    with oracle.exact_predicates():
+        ids_x, nh = oracle.pip_join(g, pe, P.verts, P.ring_off, P.poly_ring_off, with_hits=True)
+    np.testing.assert_array_equal(nh, 1)
+    ids_f = oracle.pip_join(g, pe, P.verts, P.ring_off, P.poly_ring_off)
+    assert (ids_x != ids_f).sum() > 0            # the two rules differ on some edge points
+    w = synth.pip_tiles(n_points=200_000, layer=3)
+    Q = w.polygons
+    with oracle.exact_predicates():
+        ex = oracle.pip_join(w.grid, w.points, Q.verts, Q.ring_off, Q.poly_ring_off)
+    np.testing.assert_array_equal(ex, oracle.pip_join(w.grid, w.points, Q.verts, Q.ring_off, Q.poly_ring_off))
