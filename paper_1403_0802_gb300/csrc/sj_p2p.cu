@@ -156,26 +156,32 @@ __device__ __forceinline__ void window_f32(double w, float &dn, float &up) {
     up = __double2float_ru(__dadd_rn(__dmul_rn(w, 1.0 + 1e-12), 1e-300));
 }
 
-__device__ __forceinline__ float warp_min(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(FULL, v, o));
-    return v;
+// Warp-wide min / max of a float (no NaN) in one integer reduction: flipping
+// the magnitude bits of negative floats makes signed-integer order equal
+// float order (-0 sorts just below +0).
+__device__ __forceinline__ int float_key(float v) {
+    const int i = __float_as_int(v);
+    return i ^ ((i >> 31) & 0x7fffffff);
 }
-__device__ __forceinline__ float warp_max(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(FULL, v, o));
-    return v;
-}
+__device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((k >> 31) & 0x7fffffff)); }
+__device__ __forceinline__ float warp_min(float v) { return key_float(__reduce_min_sync(FULL, float_key(v))); }
+__device__ __forceinline__ float warp_max(float v) { return key_float(__reduce_max_sync(FULL, float_key(v))); }
 
-// Refine the staged segments [0, ns) for the item's np points.
+// Refine the staged segments [0, ns) for the item's np points.  Rounds of 32
+// points take one lane per point (every lane busy, no merge); the last round,
+// of fewer than 32 points, splits each point's segments over a group of sg
+// lanes chosen by the cost model (more lanes per point, log2(sg) merges).
 template <bool FP32>
 __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, int lane) {
     using T = typename std::conditional<FP32, float, double>::type;
     const T INF = (T)__longlong_as_double(0x7ff0000000000000LL);
-    const int sg = choose_group(np, ns, 2);
-    const int lg = __ffs(sg) - 1, pg = 32 >> lg;
-    const int sub = lane & (sg - 1), grp = lane >> lg;
+    int pg = 32;
     for (int q0 = 0; q0 < np; q0 += pg) {
+        const int rem = np - q0;
+        const int sg = rem >= 32 ? 1 : choose_group(rem, ns, 2);
+        const int lg = __ffs(sg) - 1;
+        pg = 32 >> lg;
+        const int sub = lane & (sg - 1), grp = lane >> lg;
         const int q = q0 + grp;
         Best<T> st{INF, INF, -1};
         if (q < np) {
@@ -207,9 +213,11 @@ __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, in
 }
 
 // PW: per-point windows (a.win_on set; batched rounds).  The direct joins use
-// PW = false, whose code has no window load at all.
+// PW = false, whose code has no window load at all.  Eight blocks per SM is
+// the shared-memory limit already; saying so keeps the register allocator at
+// 64 registers without spills.
 template <bool FP32, bool PW>
-__global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
+__global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) {
     using T = typename std::conditional<FP32, float, double>::type;
     constexpr int SMAX = P2PSmem<FP32>::SMAX;
     extern __shared__ __align__(16) unsigned char p2p_smem_raw[];
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
         // 1. points: cell-relative FP32 coordinates, their box and magnitude
-        float bxlo = FINF, bxhi = -FINF, bylo = FINF, byhi = -FINF, pmag = 0.0f;
+        float bxlo = FINF, bxhi = -FINF, bylo = FINF, byhi = -FINF;
         for (int q = lane; q < np; q += 32) {
             const double2 p = slot_point(a, j0 + q);
             float hx, lx, hy, ly;
@@ -266,11 +274,11 @@ __global__ void __launch_bounds__(P2P_WARPS * 32) k_p2p_refine(RefineArgs a) {
             s.i1[q] = -1;
             bxlo = fminf(bxlo, rx); bxhi = fmaxf(bxhi, rx);
             bylo = fminf(bylo, ry); byhi = fmaxf(byhi, ry);
-            pmag = fmaxf(pmag, fmaxf(fabsf(rx), fabsf(ry)));
         }
         bxlo = warp_min(bxlo); bylo = warp_min(bylo);
         bxhi = warp_max(bxhi); byhi = warp_max(byhi);
-        pmag = warp_max(pmag);
+        // largest |coordinate| of the points: the larger magnitude of the box's ends
+        const float pmag = fmaxf(fmaxf(fabsf(bxlo), fabsf(bxhi)), fmaxf(fabsf(bylo), fabsf(byhi)));
         if (a.work_next) it_next = __shfl_sync(FULL, it_next, 0);
         int2 item_n = make_int2(0, 0);
         if (it_next < n_items) item_n = a.items[it_next];
