@@ -187,7 +187,7 @@ __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, in
         if (q < np) {
             if constexpr (FP32) {
                 const float2 p = s.pt[q];
-#pragma unroll 2
+#pragma unroll 1
                 for (int t = sub; t < ns; t += sg) {
                     const float4 g = s.seg[t];
                     const float2 h = s.si[t];
