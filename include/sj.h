@@ -47,7 +47,11 @@ extern "C" {
 #endif
 
 /* Uniform grid over [x0, x1) x [y0, y1) with nx * ny cells (Sec. III.A).
- * Requires finite x0 < x1, y0 < y1, 1 <= nx, ny <= 2^20 and nx * ny < 2^31 - 1. */
+ * Requires finite x0 < x1, y0 < y1, 1 <= nx, ny <= 2^20 and nx * ny <= 2^31 - 2^22.
+ * Every element count of the library (cells, points, vertices, rings,
+ * candidate and list entries) is at most 2^31 - 2^22, so that 32-bit indices
+ * of the kernels' grid-stride loops never overflow; a layer whose lists would
+ * be longer is rejected with SJ_ERR_INVALID. */
 typedef struct {
     double x0, y0, x1, y1;
     int32_t nx, ny;
@@ -130,7 +134,7 @@ typedef struct {
  *   g              host grid; every polygon MBB must lie in the closed grid box
  * The input arrays are copied; the caller may free them after return.  The
  * call synchronises `stream` (it reads validation results back).
- * Errors: SJ_ERR_INVALID (topology, NaN/inf, V >= 2^31), SJ_ERR_GRID_COVER,
+ * Errors: SJ_ERR_INVALID (topology, NaN/inf, V > 2^31 - 2^22), SJ_ERR_GRID_COVER,
  * SJ_ERR_OOM, SJ_ERR_CUDA. */
 sj_status sj_pip_layer_create(const double *verts, int64_t V, const int64_t *ring_off, int64_t R,
                               const int64_t *poly_ring_off, int32_t P, const sj_grid *g, void *stream,
@@ -161,7 +165,7 @@ sj_status sj_layer_get_candidates(const sj_layer *layer, int32_t *cand_start, in
  *   pts     dev [N, 2] f64, 16-byte aligned
  *   out_id  dev [N] int32
  *   opts    may be NULL
- * N < 2^31.  Asynchronous on stream. */
+ * N <= 2^31 - 2^22.  Asynchronous on stream. */
 sj_status sj_pip_join(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, const sj_opts *opts,
                       void *stream);
 

@@ -45,6 +45,7 @@ cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *n
                                 float4 *rec, cudaStream_t s);
 cudaError_t launch_offsets(const int *cnt, int n, int *out, int2 *block_sums, size_t cap, int *totals,
                            cudaStream_t s);
+cudaError_t launch_sum64(const int *cnt, int n, unsigned long long *total, cudaStream_t s);
 cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned long long *ky, cudaStream_t s);
 cudaError_t launch_frames(const GridDev &g, float *fx, float *fy, cudaStream_t s);
 int pip_blocks_per_sm(int form);
@@ -100,7 +101,7 @@ static bool grid_ok(const sj_grid *g) {
     if (!g) return false;
     if (!(g->nx >= 1 && g->ny >= 1)) return false;
     if (g->nx > (1 << 20) || g->ny > (1 << 20)) return false;
-    if ((int64_t)g->nx * (int64_t)g->ny > 2147483646LL) return false;
+    if ((int64_t)g->nx * (int64_t)g->ny > MAX_COUNT) return false;
     if (!(std::isfinite(g->x0) && std::isfinite(g->x1) && std::isfinite(g->y0) && std::isfinite(g->y1))) return false;
     return g->x1 > g->x0 && g->y1 > g->y0;
 }
@@ -282,7 +283,7 @@ static sj_status build_candidates(sj_layer *L, int *dbad, cudaStream_t s) {
     unsigned long long M = 0;
     CUDA_TRY(cudaMemcpyAsync(&M, total, sizeof(M), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (M > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (cell, object) candidate pairs");
+    if (M > (unsigned long long)MAX_COUNT) return fail(SJ_ERR_INVALID, "more than 2^31 - 2^22 (cell, object) candidate pairs");
     L->M = (int64_t)M;
     CUDA_TRY(dalloc(&L->cand_ids, (size_t)M));
     if (L->nobj > 0) {
@@ -353,7 +354,7 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     unsigned long long MS = 0;
     CUDA_TRY(cudaMemcpyAsync(&MS, total, sizeof(MS), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (MS > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (cell, segment) pairs");
+    if (MS > (unsigned long long)MAX_COUNT) return fail(SJ_ERR_INVALID, "more than 2^31 - 2^22 (cell, segment) pairs");
     L->MS = (int64_t)MS;
     CUDA_TRY(dalloc(&L->cseg_ids, (size_t)MS));
     CUDA_TRY(dalloc(&pairs, (size_t)MS)); tmp.p[6] = pairs;
@@ -411,6 +412,17 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     CUDA_TRY(dalloc(&totals, 8)); tmp.p[2] = totals;
     CUDA_TRY(dalloc(&bs, cap)); tmp.p[3] = bs;
     CUDA_TRY(launch_pip_boundary(a, 0, s));
+    {   // both lists' sizes in 64 bits before their 32-bit offsets
+        unsigned long long *sum = nullptr, hs[2] = {0, 0};
+        CUDA_TRY(dalloc(&sum, 2)); tmp.p[4] = sum;
+        CUDA_TRY(cudaMemsetAsync(sum, 0, 2 * sizeof(unsigned long long), s));
+        CUDA_TRY(launch_sum64(a.near_cnt, M, sum, s));
+        CUDA_TRY(launch_sum64(a.flip_cnt, M, sum + 1, s));
+        CUDA_TRY(cudaMemcpyAsync(hs, sum, sizeof(hs), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (hs[0] > (unsigned long long)MAX_COUNT || hs[1] > (unsigned long long)MAX_COUNT)
+            return fail(SJ_ERR_INVALID, "boundary lists exceed 2^31 - 2^22 entries");
+    }
     CUDA_TRY(launch_offsets(a.near_cnt, M, L->bnear_start, bs, cap, totals, s));
     CUDA_TRY(launch_offsets(a.flip_cnt, M, L->bflip_start, bs, cap, totals + 4, s));
     int tot[8] = {};
@@ -418,7 +430,6 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     CUDA_TRY(cudaStreamSynchronize(s));
     L->MN = tot[0];
     L->MF = tot[4];
-    if (tot[0] < 0 || tot[4] < 0) return fail(SJ_ERR_INVALID, "boundary lists exceed 2^31 - 1 entries");
     CUDA_TRY(dalloc(&L->bnear_ids, (size_t)L->MN));
     CUDA_TRY(dalloc(&L->bnear_rec, 2 * (size_t)L->MN));
     CUDA_TRY(dalloc(&L->bflip_keys, (size_t)L->MF));
@@ -478,7 +489,7 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     unsigned long long MR = 0;
     CUDA_TRY(cudaMemcpyAsync(&MR, total, sizeof(MR), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (MR > 2147483646ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 2 (polygon, row) slots");
+    if (MR > (unsigned long long)MAX_COUNT) return fail(SJ_ERR_INVALID, "more than 2^31 - 2^22 (polygon, row) slots");
     L->MR = (int64_t)MR;
     CUDA_TRY(dalloc(&cnt, (size_t)MR)); tmp.p[3] = cnt;
     CUDA_TRY(dalloc(&cursor, (size_t)MR)); tmp.p[4] = cursor;
@@ -488,7 +499,7 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     unsigned long long ME = 0;
     CUDA_TRY(cudaMemcpyAsync(&ME, total + 1, sizeof(ME), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (ME > 2147483647ULL) return fail(SJ_ERR_INVALID, "more than 2^31 - 1 (polygon, row, edge) entries");
+    if (ME > (unsigned long long)MAX_COUNT) return fail(SJ_ERR_INVALID, "more than 2^31 - 2^22 (polygon, row, edge) entries");
     L->ME = (int64_t)ME;
     CUDA_TRY(dalloc(&L->prow_start, (size_t)MR + 1));
     CUDA_TRY(dalloc(&L->pedge_ids, (size_t)ME));
@@ -519,7 +530,7 @@ static sj_status layer_common_checks(const double *verts, int64_t V, const sj_gr
     if (!out) return fail(SJ_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (!grid_ok(g)) return fail(SJ_ERR_INVALID, "invalid grid");
-    if (V < 0 || V > 2147483647LL) return fail(SJ_ERR_INVALID, "vertex count out of range");
+    if (V < 0 || V > MAX_COUNT) return fail(SJ_ERR_INVALID, "vertex count out of range (at most 2^31 - 2^22)");
     if (V > 0 && (!verts || !aligned16(verts))) return fail(SJ_ERR_INVALID, "verts NULL or not 16-byte aligned");
     (void)stream;
     int dev = 0;
@@ -533,7 +544,7 @@ extern "C" sj_status sj_pip_layer_create(const double *verts, int64_t V, const i
     DevInfo *di;
     sj_status st = layer_common_checks(verts, V, g, stream, out, &di);
     if (st != SJ_OK) return st;
-    if (P < 0 || R < 0 || R > 2147483646LL) return fail(SJ_ERR_INVALID, "ring or polygon count out of range");
+    if (P < 0 || R < 0 || R > MAX_COUNT) return fail(SJ_ERR_INVALID, "ring or polygon count out of range");
     if (!ring_off || !poly_ring_off) return fail(SJ_ERR_INVALID, "offset array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     LayerGuard guard{new sj_layer()};
@@ -742,7 +753,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
     if (L->kind != kind) return fail(SJ_ERR_INVALID, kind == KIND_PIP ? "not a polygon layer" : "not a polyline layer");
     if (window >= 0.0 && !(window <= L->D)) return fail(SJ_ERR_INVALID, "window must lie in [0, layer D]");
-    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (N < 0 || N > MAX_COUNT) return fail(SJ_ERR_INVALID, "N out of range (at most 2^31 - 2^22)");
     if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
     if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
     int form = o ? o->form : SJ_FP64;
@@ -874,7 +885,7 @@ extern "C" sj_status sj_p2p_join_window(const sj_layer *L, const double *pts, in
 // cell, sparser work items), so four quarter joins were measured slower.
 static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                            const sj_opts *o, void *stream) {
-    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (N < 0 || N > MAX_COUNT) return fail(SJ_ERR_INVALID, "N out of range (at most 2^31 - 2^22)");
     if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
     if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -958,7 +969,7 @@ extern "C" sj_status sj_p2p_join_host(const sj_layer *L, const double *pts, int6
 extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32_t *cell_start, int32_t *perm,
                                       void *stream) {
     if (!grid_ok(g)) return fail(SJ_ERR_INVALID, "invalid grid");
-    if (N < 0 || N > 2147483647LL) return fail(SJ_ERR_INVALID, "N out of range");
+    if (N < 0 || N > MAX_COUNT) return fail(SJ_ERR_INVALID, "N out of range (at most 2^31 - 2^22)");
     if (!cell_start || (N > 0 && (!pts || !perm))) return fail(SJ_ERR_INVALID, "NULL buffer");
     if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
     cudaStream_t s = (cudaStream_t)stream;

@@ -269,7 +269,7 @@ static cudaError_t enqueue_round(const sj_engine *E, const LayerWork *w, const D
 extern "C" sj_status sj_engine_create(int64_t max_points, int32_t max_requests, const sj_opts *o, sj_engine **out) {
     if (!out) return fail(SJ_ERR_INVALID, "out is NULL");
     *out = nullptr;
-    if (max_points < 1 || max_points > 2147483647LL) return fail(SJ_ERR_INVALID, "max_points must be in 1..2^31-1");
+    if (max_points < 1 || max_points > MAX_COUNT) return fail(SJ_ERR_INVALID, "max_points must be in 1..2^31-2^22");
     if (max_requests < 1 || max_requests > (1 << 20)) return fail(SJ_ERR_INVALID, "max_requests must be in 1..2^20");
     const int form = o ? o->form : SJ_FP64;
     if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
@@ -313,7 +313,7 @@ extern "C" sj_status sj_engine_round(sj_engine *E, const sj_request *reqs, int32
         const sj_request &r = reqs[k];
         if (!r.layer) return fail(SJ_ERR_INVALID, "request without a layer");
         if (r.layer->device != dev) return fail(SJ_ERR_INVALID, "layer belongs to another device");
-        if (r.N < 0 || r.N > 2147483647LL) return fail(SJ_ERR_INVALID, "request N out of range");
+        if (r.N < 0 || r.N > MAX_COUNT) return fail(SJ_ERR_INVALID, "request N out of range");
         if (r.N > 0 && (!r.pts || !r.out_id || !aligned16(r.pts))) return fail(SJ_ERR_INVALID, "bad request buffers");
         if (r.use_window && (r.layer->kind != KIND_P2P || !(r.window >= 0.0 && r.window <= r.layer->D)))
             return fail(SJ_ERR_INVALID, "a request window needs a polyline layer and 0 <= window <= its D");

@@ -841,6 +841,20 @@ cudaError_t launch_prow_records(const int *pedge_ids, long long ME, const int *n
     return cudaGetLastError();
 }
 
+// 64-bit sum of cnt[0..n) added to *total (checks a list's size before its
+// 32-bit offsets are taken).
+__global__ void k_sum64(const int *cnt, int n, unsigned long long *total) {
+    unsigned long long v = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v += (unsigned)cnt[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    if ((threadIdx.x & 31) == 0 && v) atomicAdd(total, v);
+}
+
+cudaError_t launch_sum64(const int *cnt, int n, unsigned long long *total, cudaStream_t s) {
+    k_sum64<<<stream_blocks(n, 256, 4096), 256, 0, s>>>(cnt, n, total);
+    return cudaGetLastError();
+}
+
 // Exclusive offsets out[0..n] of the counts cnt[0..n) (out[n] = total, also in
 // totals[0]); block_sums holds cap entries (bucket_scan_blocks(n)).
 cudaError_t launch_offsets(const int *cnt, int n, int *out, int2 *block_sums, size_t cap, int *totals,

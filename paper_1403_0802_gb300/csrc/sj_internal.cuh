@@ -11,6 +11,11 @@ namespace sj {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_CH = 128;        // largest point chunk per work item
+// Largest element count of any array the kernels index with 32-bit ints
+// (points, vertices, candidate and list entries): grids have at most 2^22
+// threads, so a grid-stride index i < MAX_COUNT never passes 2^31 - 1 when
+// it advances.
+constexpr long long MAX_COUNT = 2147483647LL - (1LL << 22);
 constexpr float U32 = 5.9604644775390625e-08f;   // 2^-24, unit roundoff of FP32
 
 // Grid with derived cell sizes (computed once on the host, FP64, rounded) and

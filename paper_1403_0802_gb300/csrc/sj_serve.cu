@@ -415,7 +415,7 @@ extern "C" sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opt
     if (p2p && p2p->kind != KIND_P2P) return fail(SJ_ERR_INVALID, "p2p is not a polyline layer");
     if (mode != SJ_SERVE_BATCHED && mode != SJ_SERVE_PER_REQUEST) return fail(SJ_ERR_INVALID, "unknown mode");
     if (hbm_budget < (int64_t)(4 * ALIGN)) return fail(SJ_ERR_INVALID, "hbm_budget too small");
-    if (round_points < 1 || round_points > 2147483647LL) return fail(SJ_ERR_INVALID, "round_points out of range");
+    if (round_points < 1 || round_points > MAX_COUNT) return fail(SJ_ERR_INVALID, "round_points out of range");
     if (max_requests < 1) return fail(SJ_ERR_INVALID, "max_requests must be >= 1");
     const int form = opts ? opts->form : SJ_FP64;
     if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");

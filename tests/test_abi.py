@@ -62,6 +62,11 @@ def test_argument_errors_are_synchronous_and_need_no_gpu(libsj):
     assert b"grid" in lib.sj_last_error()
     st = lib.sj_bucket_points(None, 0, C.byref(bad), None, None, None)
     assert st == _lib.SJ_ERR_INVALID
+    # element counts stop at 2^31 - 2^22 (32-bit grid-stride indices never overflow)
+    big = _lib.sj_grid(0.0, 0.0, 1.0, 1.0, 1 << 20, 1 << 11)       # 2^31 cells
+    assert lib.sj_bucket_points(None, 0, C.byref(big), None, None, None) == _lib.SJ_ERR_INVALID
+    e = C.c_void_p()
+    assert lib.sj_engine_create((1 << 31) - (1 << 22) + 1, 8, None, C.byref(e)) == _lib.SJ_ERR_INVALID
     for w in (-1.0, float("nan")):    # a per-call P2P window is checked before the layer is touched
         st = lib.sj_p2p_join_window(None, None, 0, w, None, None, None, None)
         assert st == _lib.SJ_ERR_INVALID
