@@ -236,6 +236,28 @@ def test_pip_empty_and_outside(api, oracle):
         np.testing.assert_array_equal(to_np(api.pip_join(layer, w.points)), -1)
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_p2p_empty_and_outside(api, oracle, form):
+    """No points; points outside the grid or NaN; a layer without polylines;
+    a window of 0 on points off every polyline."""
+    w = synth.p2p_walks(n_points=2000, n_lines=50)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        gid, gd = api.p2p_join(layer, np.zeros((0, 2)), form=form)
+        assert gid.numel() == 0 and gd.numel() == 0
+        pts = np.array([[-1.0, 5.0], [np.nan, 1.0], [1e5, 1e5], [2e5, 0.0]])
+        gid, gd = api.p2p_join(layer, pts, form=form)
+        np.testing.assert_array_equal(to_np(gid), -1)
+        assert np.isinf(to_np(gd)).all()
+        gid, gd = api.p2p_join(layer, w.points, form=form, window=0.0)
+        rid, rd, _, _ = oracle.p2p_join(w.grid, w.points, Lw.verts, Lw.line_off, 0.0)
+        np.testing.assert_array_equal(to_np(gid), rid)
+    with api.p2p_layer(np.zeros((0, 2)), np.zeros(1, np.int64), w.D, w.grid) as layer:
+        gid, gd = api.p2p_join(layer, w.points, form=form)
+        np.testing.assert_array_equal(to_np(gid), -1)
+        assert np.isinf(to_np(gd)).all()
+
+
 def test_layer_errors(api):
     from paper_1403_0802_gb300._lib import SJError, SJ_ERR_INVALID, SJ_ERR_GRID_COVER
     g = dict(x0=0.0, y0=0.0, x1=10.0, y1=10.0, nx=4, ny=4)
@@ -589,3 +611,38 @@ def test_p2p_at_scale_full_size_sampled(api, oracle):
     s.grid, s.points, s.D, s.polylines = w.grid, np.ascontiguousarray(w.points[idx]), w.D, Lw
     r = check_p2p(oracle, s, gid[idx], gd[idx], "fp32x")
     assert 0.05 < r["hit_frac"] < 1.0
+
+
+def test_pip_at_the_maximum_point_count(api, oracle):
+    """N = 2^31 - 2^22 points, the largest count a join accepts (34 GB of
+    points, about 90 GB on the device in all), against the 1,024 stars: the
+    32-bit indices of every kernel reach their limit.  A seeded 200,000-point
+    sample is checked against the oracle one by one; one point more is
+    rejected before any device work."""
+    N = (1 << 31) - (1 << 22)
+    free, _ = torch.cuda.mem_get_info()
+    if free < 120e9:
+        pytest.skip("needs about 120 GB of free device memory")
+    w = synth.pip_stars(n_points=1000)
+    P = w.polygons
+    gen = torch.Generator(device="cuda").manual_seed(20140304)
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        pts = torch.rand((N, 2), dtype=torch.float64, device="cuda", generator=gen).mul_(1e5)
+        out = torch.empty(N, dtype=torch.int32, device="cuda")
+        api.pip_join(layer, pts, out, form="fp32x")
+        idx = torch.as_tensor(np.random.default_rng(7).choice(N, SAMPLE, replace=False), device="cuda")
+        sample = pts[idx].cpu().numpy()
+        got = out[idx].cpu().numpy()
+        tail = out[-SAMPLE:].cpu().numpy()
+        tail_pts = pts[-SAMPLE:].cpu().numpy()
+        hit_frac = float((out[: 1 << 24] >= 0).float().mean())
+        from paper_1403_0802_gb300 import _lib
+        assert _lib.lib().sj_pip_join(layer.handle, pts.data_ptr(), N + 1, out.data_ptr(), None,
+                                      None) == _lib.SJ_ERR_INVALID
+        del pts, out
+        torch.cuda.empty_cache()
+    np.testing.assert_array_equal(got, oracle.pip_join(w.grid, np.ascontiguousarray(sample), P.verts, P.ring_off,
+                                                       P.poly_ring_off))
+    np.testing.assert_array_equal(tail, oracle.pip_join(w.grid, np.ascontiguousarray(tail_pts), P.verts,
+                                                        P.ring_off, P.poly_ring_off))
+    assert 0.3 < hit_frac < 0.45
