@@ -15,7 +15,7 @@ constexpr int MAX_CH = 128;        // largest point chunk per work item
 // (points, vertices, candidate and list entries): grids have at most 2^22
 // threads, so a grid-stride index i < MAX_COUNT never passes 2^31 - 1 when
 // it advances.
-constexpr long long MAX_COUNT = 2147483647LL - (1LL << 22);
+constexpr long long MAX_COUNT = (1LL << 31) - (1LL << 22);
 constexpr float U32 = 5.9604644775390625e-08f;   // 2^-24, unit roundoff of FP32
 
 // Grid with derived cell sizes (computed once on the host, FP64, rounded) and
