@@ -168,20 +168,22 @@ cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned
 // flight at once.
 constexpr int UNR = 4;
 
+// The step UNR * T can exceed the 2^22 headroom below 2^31 that the element
+// cap leaves, so the UNR kernels count in 64 bits.
 __global__ void k_cell_hist(BucketArgs a) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const int T = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
         double2 p[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             if (i < a.n) p[u] = a.pts[i];
         }
         int c[UNR], r[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             c[u] = a.g.G;
             r[u] = 0;
             if (i < a.n) {
@@ -191,7 +193,7 @@ __global__ void k_cell_hist(BucketArgs a) {
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             if (i < a.n) {
                 a.key_rank[i] = make_int2(c[u], r[u]);
                 if (a.out_id) a.out_id[i] = -1;
@@ -229,13 +231,13 @@ struct BucketApply {
 };
 
 __global__ void k_scatter(BucketArgs a) {
-    const int T = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
         int2 k[UNR];
         double2 p[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             k[u] = make_int2(a.g.G, 0);
             if (i < a.n) {
                 k[u] = a.key_rank[i];
@@ -257,14 +259,14 @@ __global__ void k_scatter(BucketArgs a) {
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             if (pos[u] >= 0) {
-                a.perm[pos[u]] = i0 + u * T;
+                a.perm[pos[u]] = (int)(i0 + u * T);
                 if (a.spts) a.spts[pos[u]] = p[u];
             }
         }
         if (a.pos) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const int i = i0 + u * T;
+                const long long i = i0 + u * T;
                 if (i < a.n) a.pos[i] = pos[u];
             }
         }
@@ -275,8 +277,8 @@ __global__ void k_scatter(BucketArgs a) {
 __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id,
                          double *out_d) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const int T = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
         int j[UNR], id[UNR];
         double d[UNR];
 #pragma unroll
@@ -288,7 +290,7 @@ __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d,
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             if (i < n) {
                 out_id[i] = id[u];
                 if (out_d) out_d[i] = d[u];
@@ -315,8 +317,8 @@ cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
 template <typename R>
 __global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, double *out_d) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const int T = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+    const long long T = (long long)gridDim.x * blockDim.x;
+    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
         int j[UNR];
         R r[UNR];
 #pragma unroll
@@ -326,7 +328,7 @@ __global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, d
             if (j[u] >= 0) r[u] = res[j[u]];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const int i = i0 + u * T;
+            const long long i = i0 + u * T;
             if (i < n) {
                 out_id[i] = j[u] >= 0 ? r[u].id : -1;
                 if (out_d) out_d[i] = j[u] >= 0 ? (double)r[u].d : inf;

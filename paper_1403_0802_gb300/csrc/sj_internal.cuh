@@ -12,9 +12,10 @@ namespace sj {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr int MAX_CH = 128;        // largest point chunk per work item
 // Largest element count of any array the kernels index with 32-bit ints
-// (points, vertices, candidate and list entries): grids have at most 2^22
-// threads, so a grid-stride index i < MAX_COUNT never passes 2^31 - 1 when
-// it advances.
+// (points, vertices, candidate and list entries): every grid-stride loop with
+// a 32-bit index advances by at most 2^22 (grids are capped below that), so an
+// index i < MAX_COUNT never passes 2^31 - 1 when it advances; loops with a
+// larger step (the unrolled bucketing and unsort kernels) count in 64 bits.
 constexpr long long MAX_COUNT = (1LL << 31) - (1LL << 22);
 constexpr float U32 = 5.9604644775390625e-08f;   // 2^-24, unit roundoff of FP32
 
