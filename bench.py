@@ -60,7 +60,7 @@ def parse():
     ap.add_argument("--form", choices=["fp32x", "fp64"], default="fp32x")
     ap.add_argument("--grid", type=int, default=0, help="filter grid cells per axis (0: the workload's)")
     ap.add_argument("--ppi", type=int, default=0, help="points per work item, 1..128 (0: library default 128)")
-    ap.add_argument("--requests", type=int, default=2000, help="serve: stream length")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: stream length")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64, e2e and CPU comparison legs")
     ap.add_argument("--oracle-full", action="store_true",
                     help="--impl reference: join the whole workload once instead of bounded steps")
@@ -478,13 +478,16 @@ def run_serve(args):
     p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
     pool_p = torch.from_numpy(wp.points).pin_memory()
     pool_l = torch.from_numpy(wl.points).pin_memory()
+    outs = {serve.PIP: (torch.empty(len(pool_p), dtype=torch.int32, pin_memory=True), None),
+            serve.P2P: (torch.empty(len(pool_l), dtype=torch.int32, pin_memory=True),
+                        torch.empty(len(pool_l), dtype=torch.float64, pin_memory=True))}
     srv = serve.Server(pip, p2p, form=args.form, round_points=6_000_000, max_requests=4096)
     arms = [("batched", args.form), ("per_request", args.form), ("per_request", "fp64")]
     for mode, form in arms:      # warm-up: workspaces, graphs, allocator pools
-        srv.run(serve.make_stream(32, 0.0, pool_p, pool_l, seed=1), mode=mode, form=form)
+        srv.run(serve.make_stream(32, 0.0, pool_p, pool_l, seed=1), mode=mode, form=form, out_pools=outs)
     # capacity of each arm with every request queued at t = 0
     sat = {f"{m}_{f}": srv.run(serve.make_stream(min(args.requests, 300), 0.0, pool_p, pool_l, seed=3),
-                               mode=m, form=f) for m, f in arms}
+                               mode=m, form=f, out_pools=outs) for m, f in arms}
     mean_pts = sat[f"batched_{args.form}"]["points"] / sat[f"batched_{args.form}"]["requests"]
     base = sat["per_request_fp64"]["points_per_s"]          # the plain FP64 one-launch-per-request form
     res = {}
@@ -492,11 +495,11 @@ def run_serve(args):
         rate = rho * base / mean_pts
         for m, f in arms:
             reqs = serve.make_stream(args.requests, rate, pool_p, pool_l, seed=7)
-            res[f"{m}_{f}_rho{rho}"] = srv.run(reqs, mode=m, form=f)
+            res[f"{m}_{f}_rho{rho}"] = srv.run(reqs, mode=m, form=f, out_pools=outs)
     fast = sat[f"per_request_{args.form}"]["points_per_s"]  # a load the FP64 form cannot sustain
     for m, f in arms[:2]:
         reqs = serve.make_stream(args.requests, 0.8 * fast / mean_pts, pool_p, pool_l, seed=7)
-        res[f"{m}_{f}_rho0.8_of_{args.form}_capacity"] = srv.run(reqs, mode=m, form=f)
+        res[f"{m}_{f}_rho0.8_of_{args.form}_capacity"] = srv.run(reqs, mode=m, form=f, out_pools=outs)
     b, p64 = res[f"batched_{args.form}_rho0.8"], res["per_request_fp64_rho0.8"]
     line = {"metric": "serving p50/p99 latency (ms) and points/s, continuous batching", "value": b["p99_ms"],
             "unit": "ms (p99)", "n_gpus": 1, "steps": args.requests, "warmup": 32, "ms_per_step": b["mean_ms"],

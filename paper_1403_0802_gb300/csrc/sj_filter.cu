@@ -169,32 +169,33 @@ cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned
 constexpr int UNR = 4;
 
 // The step UNR * T can exceed the 2^22 headroom below 2^31 that the element
-// cap leaves, so the UNR kernels count in 64 bits.
+// cap leaves, so the UNR kernels count in unsigned 32 bits: an index below
+// the cap plus a step below 2^31 stays below 2^32.
 __global__ void k_cell_hist(BucketArgs a) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const long long T = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+    const unsigned T = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
         double2 p[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
-            if (i < a.n) p[u] = a.pts[i];
+            const unsigned i = i0 + u * T;
+            if (i < (unsigned)a.n) p[u] = a.pts[i];
         }
         int c[UNR], r[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
+            const unsigned i = i0 + u * T;
             c[u] = a.g.G;
             r[u] = 0;
-            if (i < a.n) {
+            if (i < (unsigned)a.n) {
                 c[u] = point_cell(a.g, p[u].x, p[u].y);
                 if (c[u] < a.g.G) r[u] = atomicAdd(&a.cnt[c[u]], 1);
             }
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
-            if (i < a.n) {
+            const unsigned i = i0 + u * T;
+            if (i < (unsigned)a.n) {
                 a.key_rank[i] = make_int2(c[u], r[u]);
                 if (a.out_id) a.out_id[i] = -1;
                 if (a.out_d) a.out_d[i] = inf;
@@ -231,15 +232,15 @@ struct BucketApply {
 };
 
 __global__ void k_scatter(BucketArgs a) {
-    const long long T = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < a.n; i0 += UNR * T) {
+    const unsigned T = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
         int2 k[UNR];
         double2 p[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
+            const unsigned i = i0 + u * T;
             k[u] = make_int2(a.g.G, 0);
-            if (i < a.n) {
+            if (i < (unsigned)a.n) {
                 k[u] = a.key_rank[i];
                 if (a.spts) p[u] = a.pts[i];
             }
@@ -266,8 +267,8 @@ __global__ void k_scatter(BucketArgs a) {
         if (a.pos) {
 #pragma unroll
             for (int u = 0; u < UNR; ++u) {
-                const long long i = i0 + u * T;
-                if (i < a.n) a.pos[i] = pos[u];
+                const unsigned i = i0 + u * T;
+                if (i < (unsigned)a.n) a.pos[i] = pos[u];
             }
         }
     }
@@ -277,12 +278,12 @@ __global__ void k_scatter(BucketArgs a) {
 __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id,
                          double *out_d) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const long long T = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+    const unsigned T = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)n; i0 += UNR * T) {
         int j[UNR], id[UNR];
         double d[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < n) ? pos[i0 + u * T] : -1;
+        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < (unsigned)n) ? pos[i0 + u * T] : -1;
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             id[u] = j[u] >= 0 ? res_id[j[u]] : -1;
@@ -290,8 +291,8 @@ __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d,
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
-            if (i < n) {
+            const unsigned i = i0 + u * T;
+            if (i < (unsigned)n) {
                 out_id[i] = id[u];
                 if (out_d) out_d[i] = d[u];
             }
@@ -317,19 +318,19 @@ cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
 template <typename R>
 __global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, double *out_d) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
-    const long long T = (long long)gridDim.x * blockDim.x;
-    for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < n; i0 += UNR * T) {
+    const unsigned T = gridDim.x * blockDim.x;
+    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)n; i0 += UNR * T) {
         int j[UNR];
         R r[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < n) ? pos[i0 + u * T] : -1;
+        for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < (unsigned)n) ? pos[i0 + u * T] : -1;
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
             if (j[u] >= 0) r[u] = res[j[u]];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const long long i = i0 + u * T;
-            if (i < n) {
+            const unsigned i = i0 + u * T;
+            if (i < (unsigned)n) {
                 out_id[i] = j[u] >= 0 ? r[u].id : -1;
                 if (out_d) out_d[i] = j[u] >= 0 ? (double)r[u].d : inf;
             }

@@ -130,11 +130,14 @@ __device__ __forceinline__ bool orient32(float px, float py, float lx, float ly,
 template <bool FP32>
 __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, const RefineArgs &a, int j0, int np,
                                                           int ns, int lane, unsigned &c_fb) {
-    const int sg = choose_group(np, ns, 0);
-    const int lg = __ffs(sg) - 1, pg = 32 >> lg;
-    const int sub = lane & (sg - 1), grp = lane >> lg;
     unsigned long long tests = 0;
-    for (int q0 = 0; q0 < np; q0 += pg) {
+    int pg = 32;
+    for (int q0 = 0; q0 < np; q0 += pg) {   // one lane per point while 32 remain, then lane groups
+        const int rem = np - q0;
+        const int sg = rem >= 32 ? 1 : choose_group(rem, ns, 0);
+        const int lg = __ffs(sg) - 1;
+        pg = 32 >> lg;
+        const int sub = lane & (sg - 1), grp = lane >> lg;
         const int q = q0 + grp;
         const bool act = q < np && s.found[q] < 0;
         const unsigned actb = __ballot_sync(FULL, act && sub == 0);
@@ -182,7 +185,7 @@ __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, cons
 }
 
 template <bool FP32>
-__global__ void __launch_bounds__(PIP_WARPS * 32) k_pip_refine(RefineArgs a) {
+__global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) {
     constexpr int SMAX = PipSmem<FP32>::SMAX;
     extern __shared__ __align__(16) unsigned char pip_smem_raw[];
     const int lane = lane_id(), w = threadIdx.x >> 5;

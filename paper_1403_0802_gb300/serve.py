@@ -41,6 +41,7 @@ class Request:
     out_id: torch.Tensor | None = None    # pinned host int32 [N]
     out_d: torch.Tensor | None = None     # pinned host float64 [N] (P2P)
     window: float | None = None           # P2P: window of this request (None = the layer's D)
+    off: int = 0                          # first point's index in its pool
 
     @property
     def n(self) -> int:
@@ -68,7 +69,7 @@ def make_stream(n_requests: int, rate_per_s: float, pool_pip: torch.Tensor, pool
         n = min(n, pool.shape[0])
         off = int(rng.integers(0, pool.shape[0] - n + 1))
         win = float(p2p_windows[int(rng.integers(0, len(p2p_windows)))]) if (p2p_windows and kind == P2P) else None
-        reqs.append(Request(k, float(t[k]), kind, pool[off:off + n], window=win))
+        reqs.append(Request(k, float(t[k]), kind, pool[off:off + n], window=win, off=off))
     return reqs
 
 
@@ -102,19 +103,29 @@ class Server:
         L.check(L.lib().sj_server_get_stats(self.handle, C.byref(s)), "sj_server_get_stats")
         return {k: getattr(s, k) for k, _ in s._fields_}
 
-    def run(self, requests: list[Request], mode: str = "batched", form: str | None = None) -> dict:
+    def run(self, requests: list[Request], mode: str = "batched", form: str | None = None,
+            out_pools: dict | None = None) -> dict:
         """Replay `requests` on the server: each is submitted up front with its
         arrival time (seconds from now) as not_before, so the native worker
         admits it then; returns latency (results in host memory - arrival) and
-        throughput statistics."""
+        throughput statistics.  out_pools ({kind: (ids, distances or None)},
+        pinned host tensors as long as the point pools) makes each request's
+        outputs the slice of the pool at its points' offset instead of buffers
+        of its own: requests that share points then write the same values to
+        the same bytes, so long streams need no memory per request."""
         assert mode in ("batched", "per_request")
         lib = L.lib()
         L.check(lib.sj_server_set_mode(self.handle, L.SJ_SERVE_BATCHED if mode == "batched" else
                                        L.SJ_SERVE_PER_REQUEST, api.FORMS[form or self.form]), "sj_server_set_mode")
         order = sorted(requests, key=lambda r: r.arrival)
         for r in order:
-            r.out_id = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
-            r.out_d = torch.empty(r.n, dtype=torch.float64, pin_memory=True) if r.kind == P2P else None
+            if out_pools is not None:
+                ids, ds = out_pools[r.kind]
+                r.out_id = ids[r.off:r.off + r.n]
+                r.out_d = ds[r.off:r.off + r.n] if (r.kind == P2P and ds is not None) else None
+            else:
+                r.out_id = torch.empty(r.n, dtype=torch.int32, pin_memory=True)
+                r.out_d = torch.empty(r.n, dtype=torch.float64, pin_memory=True) if r.kind == P2P else None
             r.t_done = math.nan
         st0 = self.stats()
         L.check(lib.sj_server_reset_maxima(self.handle), "sj_server_reset_maxima")
