@@ -69,7 +69,10 @@ typedef struct {
 } sj_server_stats;
 
 /* Create a server on the current device (this also builds the engine's
- * workspace and graph for each layer, so that no request waits for them).
+ * workspace and graph for each layer, and grows the device's default
+ * stream-ordered memory pool to the largest direct join, so that no request
+ * waits for them; the server sets that pool's release threshold to keep its
+ * memory, an attribute of this process's pool that stays after destroy).
  * pip / p2p: resident layers (either
  * may be NULL if no request of that kind is submitted; they must outlive the
  * server).  opts: form and points per work item of every round (NULL = FP64,

@@ -474,10 +474,20 @@ extern "C" sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opt
             r.out_d = k == 1 ? (double *)(tmp + 512) : nullptr;
             st = sj_engine_round(S->engine, &r, 1, S->compute);
         }
-        // Direct joins take their scratch from the stream-ordered pool (which
-        // keeps freed memory): reserve the largest one now (a request of
-        // round_points points needs under 64 B per point plus per-cell arrays)
-        // so that the pool never grows while requests are served.
+        // Direct joins take their scratch from the device's stream-ordered
+        // pool.  By default the pool hands freed memory back at every
+        // synchronising call (the engine waits on events), and the next join
+        // then grows it again (milliseconds for hundreds of MB).  The server
+        // makes the pool keep what it holds (a process-wide attribute of this
+        // device's default pool) and reserves the largest join now (a request
+        // of round_points points needs under 64 B per point plus per-cell
+        // arrays), so that the pool never grows while requests are served.
+        cudaMemPool_t pool = nullptr;
+        if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+        if (e == cudaSuccess) {
+            unsigned long long keep = ~0ULL;   // the attribute is a 64-bit unsigned value
+            e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
         void *big = nullptr;
         if (e == cudaSuccess)
             e = cudaMallocAsync(&big, (size_t)round_points * 64 + ((size_t)64 << 20), S->compute);
