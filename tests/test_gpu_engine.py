@@ -134,3 +134,28 @@ def test_round_limits(setup):
             with pytest.raises(SJError) as e:
                 eng.round([bad])                                    # windows: P2P only, within [0, D]
             assert e.value.status == SJ_ERR_INVALID
+
+
+def test_rounds_on_the_multi_ring_layer(setup):
+    """PIP rounds against the multi-ring layer (tiles with island holes and the
+    islands) equal direct joins bit for bit in both forms, island points included."""
+    api = setup[0]
+    w = synth.pip_tiles(n_points=300_000, layer=3)
+    P = w.polygons
+    pts_all = torch.as_tensor(w.points, device="cuda")
+    stream = torch.cuda.Stream()
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        for form in ("fp64", "fp32x"):
+            with api.Engine(max_points=300_000, max_requests=16, form=form) as eng:
+                cuts = [0, 1, 1000, 50_000, 120_000, 300_000]
+                reqs = [(layer, pts_all[a:b].contiguous(), torch.full((b - a,), 99, dtype=torch.int32, device="cuda"),
+                         None) for a, b in zip(cuts[:-1], cuts[1:])]
+                stream.wait_stream(torch.cuda.current_stream())
+                with torch.cuda.stream(stream):
+                    eng.round(reqs, stream)
+                stream.synchronize()
+                got = torch.cat([r[2] for r in reqs])
+                ref = api.pip_join(layer, pts_all, form=form)
+                torch.cuda.synchronize()
+                assert torch.equal(got, ref), form
+                assert int((ref >= 40_000).sum()) > 0           # some points answer an island
