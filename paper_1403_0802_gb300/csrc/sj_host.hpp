@@ -69,6 +69,7 @@ struct sj_layer {
     unsigned long long *cell_keys = nullptr;   // [nx + 1 + ny + 1] threshold tables of point_cell
     float *frames = nullptr;                   // [nx + ny] FP32 cell frame origins
     double xmax = 0.0;                         // largest |coordinate| of the grid box
+    int64_t max_obj_verts = 0;                 // vertices of the largest polygon / polyline
     float Df = 0.0f, Ddn = 0.0f, Dup = 0.0f;   // FP32 forms of D (nearest, rounded down, rounded up)
     mutable std::atomic<long long> joins{0};
     mutable std::atomic<long long> points{0};

@@ -180,6 +180,7 @@ struct RefineArgs {
     const int2 *items;       // (cell, first point of the chunk within the cell)
     const int *n_items;      // device count
     int *work_next;          // zeroed device counter handing out items (or null: fixed stride)
+    int claim;               // consecutive items a warp takes per counter update (>= 1)
     const int *cell_start;   // [G + 1] sorted point ranges
     const int *perm;         // sorted slot -> input index
     const double2 *spts;     // sorted points (FP64), or null: the point of slot j is pts[perm[j]]

@@ -236,11 +236,16 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
     // item), else in a fixed stride.
     // The next item's record and its cell's point range are loaded while the
     // current item is refined, off the per-item chain of dependent loads.
-    int it = blockIdx.x * P2P_WARPS + w;
+    // A warp takes a.claim consecutive items per counter update: consecutive
+    // items are mostly chunks of one cell, whose segment records are then
+    // still in L1 for the second chunk.
+    const int claim = a.claim > 1 ? a.claim : 1;
+    int it = blockIdx.x * P2P_WARPS + w, it_end = it + 1;
     if (a.work_next) {
         int t0 = 0;
-        if (lane == 0) t0 = atomicAdd(a.work_next, 1);
+        if (lane == 0) t0 = atomicAdd(a.work_next, claim);
         it = __shfl_sync(FULL, t0, 0);
+        it_end = it + claim;
     }
     int2 item = make_int2(0, 0);
     int cs0 = 0, cs1 = 0;
@@ -251,7 +256,11 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
     }
     while (it < n_items) {
         int it_next = it + gridDim.x * P2P_WARPS;
-        if (a.work_next && lane == 0) it_next = atomicAdd(a.work_next, 1);
+        const bool in_claim = it + 1 < it_end;
+        if (a.work_next) {
+            if (in_claim) it_next = it + 1;
+            else if (lane == 0) it_next = atomicAdd(a.work_next, claim);
+        }
         ++c_items;
         const int c = item.x;
         const int j0 = cs0 + item.y;
@@ -280,6 +289,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
         // largest |coordinate| of the points: the larger magnitude of the box's ends
         const float pmag = fmaxf(fmaxf(fabsf(bxlo), fabsf(bxhi)), fmaxf(fabsf(bylo), fabsf(byhi)));
         if (a.work_next) it_next = __shfl_sync(FULL, it_next, 0);
+        const int end_next = in_claim ? it_end : it_next + (a.work_next ? claim : 1);
         int2 item_n = make_int2(0, 0);
         if (it_next < n_items) item_n = a.items[it_next];
         float mag = pmag;   // FP32X: largest |cell-relative coordinate| refined for this item
@@ -393,6 +403,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
         }
         __syncwarp();
         it = it_next;
+        it_end = end_next;
         item = item_n;
         cs0 = cs0n;
         cs1 = cs1n;

@@ -199,15 +199,23 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
     // Items come from a device counter when a.work_next is set (the next index
     // is fetched at the start of an item, so its latency hides behind the
     // item), else in a fixed stride.
-    int it = blockIdx.x * PIP_WARPS + w;
+    // a.claim consecutive items per counter update (mostly chunks of one
+    // cell, whose staged records are then still in L1).
+    const int claim = a.claim > 1 ? a.claim : 1;
+    int it = blockIdx.x * PIP_WARPS + w, it_end = it + 1;
     if (a.work_next) {
         int t0 = 0;
-        if (lane == 0) t0 = atomicAdd(a.work_next, 1);
+        if (lane == 0) t0 = atomicAdd(a.work_next, claim);
         it = __shfl_sync(FULL, t0, 0);
+        it_end = it + claim;
     }
     while (it < n_items) {
         int it_next = it + gridDim.x * PIP_WARPS;
-        if (a.work_next && lane == 0) it_next = atomicAdd(a.work_next, 1);
+        const bool in_claim = it + 1 < it_end;
+        if (a.work_next) {
+            if (in_claim) it_next = it + 1;
+            else if (lane == 0) it_next = atomicAdd(a.work_next, claim);
+        }
         ++c_items;
         const int2 item = a.items[it];
         const int c = item.x;
@@ -376,7 +384,9 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
             if (f >= 0) ++c_hits;
         }
         __syncwarp();
-        it = a.work_next ? __shfl_sync(FULL, it_next, 0) : it_next;
+        it_next = a.work_next ? __shfl_sync(FULL, it_next, 0) : it_next;
+        it_end = in_claim ? it_end : it_next + (a.work_next ? claim : 1);
+        it = it_next;
     }
     if (a.stats) {
         c_fb = __reduce_add_sync(FULL, c_fb);
