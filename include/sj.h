@@ -75,17 +75,21 @@ enum {
                      distance error is bounded per point                           */
 };
 
-/* Launch form. */
+/* Launch form.  Every join's refinement is one persistent launch whose warps
+ * take work items from a device counter (cost-balanced); both values select
+ * that code and give the same results.  Batched rounds of many requests are
+ * the sj_engine_* calls below. */
 enum {
     SJ_PER_REQUEST = 0, /* one pass of kernels per call                           */
-    SJ_PERSISTENT = 1   /* persistent, cost-balanced refinement (same results)    */
+    SJ_PERSISTENT = 1   /* same kernels (accepted for callers that ask for it)    */
 };
 
 /* Join options; a zeroed struct (or NULL) selects the defaults. */
 typedef struct {
     int32_t form;            /* SJ_FP64 (default) or SJ_FP32X                       */
     int32_t launch;          /* SJ_PER_REQUEST (default) or SJ_PERSISTENT           */
-    int32_t block;           /* threads per refinement block (multiple of 32), 0 = default */
+    int32_t block;           /* reserved, 0 (refinement blocks are 4 warps; the grid
+                                is SMs x resident blocks, from the occupancy)      */
     int32_t pts_per_item;    /* points per work item, 1..128, 0 = default (128)    */
     int32_t edges_per_chunk; /* reserved, 0                                         */
     int32_t flags;           /* SJ_FLAG_* bits                                      */
