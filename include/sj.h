@@ -207,6 +207,11 @@ sj_status sj_pip_join_host(const sj_layer *layer, const double *pts, int64_t N, 
 sj_status sj_p2p_join_host(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                            const sj_opts *opts, void *stream);
 
+/* sj_p2p_join_window from HOST buffers (as sj_p2p_join_host, with the
+ * window of sj_p2p_join_window).  Errors: those of both. */
+sj_status sj_p2p_join_window_host(const sj_layer *layer, const double *pts, int64_t N, double window,
+                                  int32_t *out_id, double *out_d, const sj_opts *opts, void *stream);
+
 /* Point bucketing alone (Sec. III.A, Fig. 1 top-left: sort points by cell id,
  * VGC/VGI vectors): cell_start [G + 1] int32 dev gets the exclusive prefix sum
  * of per-cell point counts (cell_start[G] = in-grid points) and perm [N] int32

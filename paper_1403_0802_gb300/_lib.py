@@ -79,6 +79,7 @@ SIGNATURES = {
     "sj_p2p_join_window": (C.c_int, [_P, _P, _I64, C.c_double, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_pip_join_host": (C.c_int, [_P, _P, _I64, _P, C.POINTER(sj_opts), _P]),
     "sj_p2p_join_host": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
+    "sj_p2p_join_window_host": (C.c_int, [_P, _P, _I64, C.c_double, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_p2p_join_noalloc": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_bucket_points": (C.c_int, [_P, _I64, C.POINTER(sj_grid), _P, _P, _P]),
     "sj_layer_get_stats": (C.c_int, [_P, C.POINTER(sj_run_stats)]),

@@ -192,16 +192,20 @@ def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, 
 
 
 def p2p_join_host(layer: Layer, pts, out_id=None, out_d=None, form: str = "fp64", stream=None,
-                  pts_per_item: int = 0):
-    """Same as p2p_join from host memory (copies in and out; synchronous)."""
+                  pts_per_item: int = 0, window: float | None = None):
+    """Same as p2p_join from host memory (copies in and out; synchronous); window as in p2p_join."""
     p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
     n = p.shape[0]
     out_id = np.empty(n, np.int32) if out_id is None else out_id
     out_d = np.empty(n, np.float64) if out_d is None else out_d
     o = _opts(form, pts_per_item=pts_per_item)
     ptr = lambda a: a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
-    L.check(L.lib().sj_p2p_join_host(layer.handle, ptr(p), n, ptr(out_id), ptr(out_d), C.byref(o), _stream(stream)),
-            "sj_p2p_join_host")
+    if window is None:
+        L.check(L.lib().sj_p2p_join_host(layer.handle, ptr(p), n, ptr(out_id), ptr(out_d), C.byref(o),
+                                         _stream(stream)), "sj_p2p_join_host")
+    else:
+        L.check(L.lib().sj_p2p_join_window_host(layer.handle, ptr(p), n, float(window), ptr(out_id), ptr(out_d),
+                                                C.byref(o), _stream(stream)), "sj_p2p_join_window_host")
     return out_id, out_d
 
 

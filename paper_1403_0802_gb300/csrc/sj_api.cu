@@ -901,12 +901,12 @@ extern "C" sj_status sj_p2p_join_window(const sj_layer *L, const double *pts, in
 // three chunks: every chunk is a full join with fixed costs (scans over every
 // cell, sparser work items), so four quarter joins were measured slower.
 static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64_t N, int32_t *out_id, double *out_d,
-                           const sj_opts *o, void *stream) {
+                           const sj_opts *o, void *stream, double window = -1.0) {
     if (N < 0 || N > MAX_COUNT) return fail(SJ_ERR_INVALID, "N out of range (at most 2^31 - 2^22)");
     if (N > 0 && (!pts || !out_id)) return fail(SJ_ERR_INVALID, "NULL buffer");
     if (!L) return fail(SJ_ERR_INVALID, "layer is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    if (N == 0) return join_impl(L, kind, nullptr, 0, nullptr, nullptr, o, stream);
+    if (N == 0) return join_impl(L, kind, nullptr, 0, nullptr, nullptr, o, stream, window);
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     DevInfo *di;
@@ -948,7 +948,7 @@ static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64
         if (e == cudaSuccess) e = cudaEventRecord(copied, t_in);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(t_cmp, copied, 0);
         if (e != cudaSuccess) break;
-        st = join_impl(L, kind, dp + 2 * off, n, dI + off, dD ? dD + off : nullptr, o, t_cmp);
+        st = join_impl(L, kind, dp + 2 * off, n, dI + off, dD ? dD + off : nullptr, o, t_cmp, window);
         if (st != SJ_OK) break;
         e = cudaEventRecord(joined, t_cmp);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(t_out, joined, 0);
@@ -981,6 +981,13 @@ extern "C" sj_status sj_pip_join_host(const sj_layer *L, const double *pts, int6
 extern "C" sj_status sj_p2p_join_host(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                                       const sj_opts *o, void *stream) {
     return join_host(L, KIND_P2P, pts, N, out_id, out_d, o, stream);
+}
+
+extern "C" sj_status sj_p2p_join_window_host(const sj_layer *L, const double *pts, int64_t N, double window,
+                                             int32_t *out_id, double *out_d, const sj_opts *o, void *stream) {
+    if (!(window >= 0.0)) return fail(SJ_ERR_INVALID, "window must lie in [0, layer D]");   // NaN too
+    if (L && L->kind == KIND_P2P && !(window <= L->D)) return fail(SJ_ERR_INVALID, "window must lie in [0, layer D]");
+    return join_host(L, KIND_P2P, pts, N, out_id, out_d, o, stream, window);
 }
 
 extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32_t *cell_start, int32_t *perm,

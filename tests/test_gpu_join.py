@@ -435,6 +435,31 @@ def test_p2p_window_per_call(api, oracle, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
+def test_p2p_window_from_host_buffers(api, oracle, form):
+    """sj_p2p_join_window_host (two pipelined chunks at 3 M points) equals the
+    device window join: FP64 bit for bit; FP32X ids to near-ties and distances
+    within the certified bound (a point's FP64 recheck can depend on the other
+    points of its work item, which the chunks change)."""
+    w = synth.p2p_walks(n_points=3_000_000, n_lines=20_000)
+    Lw = w.polylines
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        for win in (30.0, w.D):
+            hid, hd = api.p2p_join_host(layer, w.points, form=form, window=win)
+            gid, gd = api.p2p_join(layer, w.points, form=form, window=win)
+            gid, gd = to_np(gid), to_np(gd)
+            if form == "fp64":
+                np.testing.assert_array_equal(hid, gid)
+                np.testing.assert_array_equal(hd, gd)
+            else:
+                assert (gid == hid).mean() > 0.9999
+                both = (gid >= 0) & (gid == hid)
+                assert np.all(np.abs(gd[both] - hd[both]) <= 1e-3 * np.maximum(gd[both], 1.0))
+            assert np.all(hd[hid >= 0] <= win)
+        with pytest.raises(Exception):
+            api.p2p_join_host(layer, w.points[:10], form=form, window=w.D * 2)
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("win", [25.0, 50.0])
 def test_p2p_window_per_call_at_cell_boundaries(api, oracle, form, win):
     """Windows smaller than the layer's D = 100 m on the axis-aligned 25 m
