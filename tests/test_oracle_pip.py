@@ -47,14 +47,21 @@ def dyadic_lattice(lo, hi, step):
 GRID_SMALL = dict(x0=-16.0, y0=-16.0, x1=16.0, y1=16.0, nx=8, ny=8)
 
 
+@pytest.mark.parametrize("exact", [False, True], ids=["fp64", "exact"])
 @pytest.mark.parametrize("shape", json.load(open(os.path.join(HERE, "golden", "pip_shapes.json")))["shapes"],
                          ids=lambda s: s["name"])
-def test_closed_form_regions(oracle, shape):
+def test_closed_form_regions(oracle, shape, exact):
+    """The closed-form regions hold under both predicate modes (the dyadic
+    lattice makes every FP64 step exact, so the two rules must agree)."""
     verts, ro, pro = layer_from_rings([shape["rings"]])
     pts = dyadic_lattice(-1.0, 8.0, 0.25)
     expect = np.where(in_region(shape["region"], pts[:, 0], pts[:, 1]), 0, -1)
-    got_b = oracle.pip_brute(GRID_SMALL, pts, verts, ro, pro)
-    got_g = oracle.pip_join(GRID_SMALL, pts, verts, ro, pro)
+    oracle._load().or_set_exact(1 if exact else 0)
+    try:
+        got_b = oracle.pip_brute(GRID_SMALL, pts, verts, ro, pro)
+        got_g = oracle.pip_join(GRID_SMALL, pts, verts, ro, pro)
+    finally:
+        oracle._load().or_set_exact(0)
     bad = np.flatnonzero(got_b != expect)
     assert bad.size == 0, (shape["name"], pts[bad[:5]], got_b[bad[:5]], expect[bad[:5]])
     np.testing.assert_array_equal(got_g, expect)
