@@ -126,6 +126,9 @@ typedef struct {
                                 edge_tests is what remains after the exact
                                 per-item prune (edges that cannot straddle /
                                 segments farther than D from every point)        */
+    int64_t census_tests;     /* sj_pip_census totals since the last reset: the  */
+    int64_t census_straddles; /* edges of the points' candidate polygons, and how
+                                 many of them straddle the point's y              */
 } sj_run_stats;
 
 /* Build a resident polygon layer and its candidate lists (Sec. III.A: MBB of
@@ -220,6 +223,18 @@ sj_status sj_p2p_join_window_host(const sj_layer *layer, const double *pts, int6
 sj_status sj_bucket_points(const double *pts, int64_t N, const sj_grid *g, int32_t *cell_start, int32_t *perm,
                            void *stream);
 
+/* Census of the algorithmic PIP work (a measurement pass, not a join; used
+ * for the arithmetic roofline of the refinement, whose per-edge cost is the
+ * straddle test of Sec. III.C plus the orientation test for the edges that
+ * straddle the point's y).  For every in-grid point of pts (dev [N, 2] f64)
+ * against the candidate polygons of its cell: out[0] = their edges (every
+ * ring), out[1] = how many of those edges straddle the point's y, i.e.
+ * (a.y > p.y) != (b.y > p.y).  out is a HOST int64 [2]; both are also added to
+ * the layer's census_tests / census_straddles counters.  Synchronises
+ * `stream`.  Errors: SJ_ERR_INVALID (NULL, not a polygon layer, N out of
+ * range), SJ_ERR_CUDA. */
+sj_status sj_pip_census(const sj_layer *layer, const double *pts, int64_t N, int64_t *out, void *stream);
+
 /* Counters of the joins run on `layer` (synchronises the device). */
 sj_status sj_layer_get_stats(const sj_layer *layer, sj_run_stats *out);
 sj_status sj_layer_reset_stats(sj_layer *layer);
@@ -290,8 +305,10 @@ sj_status sj_engine_destroy(sj_engine *engine);
  *   cells, else SJ_ERR_INVALID with a message; pts_per_item and flags in opts
  *   are ignored (64 points per item, no timing events).
  * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the previous call's
+ * device, with that device current) and keeps it for the life of the process;
+ * make that first call before any stream capture.  A device reset
+ * (cudaDeviceReset) invalidates the kept address: do not call this entry point
+ * again in a process that has reset the device.  All calls share the array and it keeps the previous call's
  * contents (the counters that must start at zero are cleared on `stream` at
  * the start of each call): calls whose kernels overlap on the GPU race, so
  * issue them on one stream or order them with events.  Asynchronous on

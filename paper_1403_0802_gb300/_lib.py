@@ -33,7 +33,8 @@ class sj_layer_info(C.Structure):
 class sj_run_stats(C.Structure):
     _fields_ = [("joins", C.c_int64), ("points", C.c_int64), ("items", C.c_int64), ("pairs", C.c_int64),
                 ("edge_tests", C.c_int64), ("fallbacks", C.c_int64), ("hits", C.c_int64),
-                ("refine_launches", C.c_int64), ("refine_ms", C.c_double), ("algo_tests", C.c_int64)]
+                ("refine_launches", C.c_int64), ("refine_ms", C.c_double), ("algo_tests", C.c_int64),
+                ("census_tests", C.c_int64), ("census_straddles", C.c_int64)]
 
 
 class sj_peak_rates(C.Structure):
@@ -83,6 +84,7 @@ SIGNATURES = {
     "sj_p2p_join_noalloc": (C.c_int, [_P, _P, _I64, _P, _P, C.POINTER(sj_opts), _P]),
     "sj_bucket_points": (C.c_int, [_P, _I64, C.POINTER(sj_grid), _P, _P, _P]),
     "sj_layer_get_stats": (C.c_int, [_P, C.POINTER(sj_run_stats)]),
+    "sj_pip_census": (C.c_int, [_P, _P, _I64, _P, _P]),
     "sj_layer_reset_stats": (C.c_int, [_P]),
     "sj_last_error": (C.c_char_p, []),
     "sj_version": (C.c_char_p, []),

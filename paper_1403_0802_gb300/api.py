@@ -178,6 +178,15 @@ def p2p_join_noalloc(layer: Layer, pts, out_id: torch.Tensor, out_d: torch.Tenso
     return out_id, out_d
 
 
+def pip_census(layer: Layer, pts, stream=None) -> tuple[int, int]:
+    """(edges of the candidate polygons, edges straddling the point's y),
+    summed over the points: the algorithmic PIP work (sj_pip_census)."""
+    p = _points(pts)
+    out = (C.c_int64 * 2)()
+    L.check(L.lib().sj_pip_census(layer.handle, _ptr(p), p.shape[0], out, _stream(stream)), "sj_pip_census")
+    return int(out[0]), int(out[1])
+
+
 def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, form: str = "fp64",
                   stream=None, pts_per_item: int = 0) -> np.ndarray:
     """Same as pip_join from host memory (copies in and out; synchronous)."""

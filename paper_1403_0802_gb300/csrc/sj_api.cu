@@ -699,6 +699,8 @@ extern "C" sj_status sj_layer_get_stats(const sj_layer *L, sj_run_stats *out) {
     out->fallbacks = (int64_t)h[ST_FALLBACK];
     out->hits = (int64_t)h[ST_HITS];
     out->algo_tests = (int64_t)h[ST_ALGO];
+    out->census_tests = L->census_tests.load();
+    out->census_straddles = L->census_straddles.load();
     return SJ_OK;
 }
 
@@ -711,6 +713,8 @@ extern "C" sj_status sj_layer_reset_stats(sj_layer *L) {
     L->refine_launches = 0;
     L->joins = 0;
     L->points = 0;
+    L->census_tests = 0;
+    L->census_straddles = 0;
     return SJ_OK;
 }
 
@@ -1035,6 +1039,32 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
     return SJ_OK;
 }
 
+extern "C" sj_status sj_pip_census(const sj_layer *L, const double *pts, int64_t N, int64_t *out, void *stream) {
+    if (!L || !out) return fail(SJ_ERR_INVALID, "NULL argument");
+    if (L->kind != KIND_PIP) return fail(SJ_ERR_INVALID, "not a polygon layer");
+    if (N < 0 || N > MAX_COUNT) return fail(SJ_ERR_INVALID, "N out of range (at most 2^31 - 2^22)");
+    if (N > 0 && (!pts || !aligned16(pts))) return fail(SJ_ERR_INVALID, "pts NULL or not 16-byte aligned");
+    out[0] = out[1] = 0;
+    if (N == 0) return SJ_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *d = nullptr, h[2] = {0, 0};
+    CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(h), s));
+    RefineArgs ra{};
+    fill_refine(L, ra);
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
+    if (e == cudaSuccess) e = launch_pip_census(ra, (const double2 *)pts, (int)N, d, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, s);
+    cudaError_t e2 = cudaFreeAsync(d, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "census");
+    if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
+    out[0] = (int64_t)h[0];
+    out[1] = (int64_t)h[1];
+    L->census_tests += out[0];
+    L->census_straddles += out[1];
+    return SJ_OK;
+}
+
 extern "C" const char *sj_last_error(void) { return g_err.c_str(); }
 
 extern "C" const char *sj_version(void) { return "sj 0.1 (sm_103a)"; }
@@ -1099,6 +1129,8 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     if (N > 0 && !aligned16(pts)) return fail(SJ_ERR_INVALID, "pts not 16-byte aligned");
     const int form = o ? o->form : SJ_FP64;
     if (form != SJ_FP64 && form != SJ_FP32X) return fail(SJ_ERR_INVALID, "unknown form");
+    if (form == SJ_FP32X && L->xmax > 1e30)
+        return fail(SJ_ERR_INVALID, "SJ_FP32X needs grid coordinates below 1e30 in magnitude; use SJ_FP64");
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev != L->device) return fail(SJ_ERR_INVALID, "layer belongs to another device");
@@ -1109,6 +1141,8 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     char *base = nullptr;
     st = noalloc_scratch(dev, &base);
     if (st != SJ_OK) return st;
+    L->joins++;
+    L->points += N;
     if (N == 0) return SJ_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const int G = L->g.G;
@@ -1153,9 +1187,10 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     ra.out_d = out_d;
     ra.fb = b.fb;
     ra.n_fb = b.totals + 2;
+    // items from the device counter, as in join_impl (totals[3], zeroed above)
+    ra.work_next = b.totals + 3;
+    ra.claim = (N >= 2LL * NOALLOC_CH * (long long)G) ? 2 : 1;
     CUDA_TRY(launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s));
     if (need_fb) CUDA_TRY(launch_p2p_recheck(ra, di->sms * 4, s));
-    L->joins++;
-    L->points += N;
     return SJ_OK;
 }

@@ -73,6 +73,8 @@ struct sj_layer {
     float Df = 0.0f, Ddn = 0.0f, Dup = 0.0f;   // FP32 forms of D (nearest, rounded down, rounded up)
     mutable std::atomic<long long> joins{0};
     mutable std::atomic<long long> points{0};
+    mutable std::atomic<long long> census_tests{0};       // sj_pip_census totals since the last reset
+    mutable std::atomic<long long> census_straddles{0};
     // SJ_FLAG_TIME_REFINE: event pairs recorded around refinement launches,
     // resolved (and destroyed) by sj_layer_get_stats.
     mutable std::mutex ev_mu;

@@ -269,6 +269,8 @@ cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const i
 cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);
 cudaError_t launch_p2p_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);
 cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s);
+cudaError_t launch_pip_census(const RefineArgs &a, const double2 *pts, int n, unsigned long long *out,
+                              cudaStream_t s);
 
 struct BucketArgs {
     GridDev g;

@@ -587,6 +587,47 @@ cudaError_t launch_pip_flips(const int *flip_start, int M, unsigned long long *k
     return cudaGetLastError();
 }
 
+// Census of the algorithmic PIP work (a measurement pass, not part of a
+// join): for every in-grid point, out[0] += the edges of its cell's candidate
+// polygons (every ring), out[1] += how many of them straddle the point's y
+// under the crossing rule's straddle test (Sec. III.C).  Only an edge of a
+// candidate's list for the point's grid row can straddle it (the row lists are
+// exact), so the straddles are counted over those lists.  One thread per point.
+__global__ void k_pip_census(RefineArgs a, const double2 *pts, int n, unsigned long long *out) {
+    unsigned long long e = 0, st = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double2 p = pts[i];
+        const int c = point_cell(a.g, p.x, p.y);
+        if (c >= a.g.G) continue;
+        const int iy = c / a.g.nx;
+        for (int k = a.cand_start[c]; k < a.cand_start[c + 1]; ++k) {
+            const int P = a.cand_ids[k];
+            e += (unsigned long long)(a.obj_voff[P + 1] - a.obj_voff[P]);
+            const int slot = a.prow_base[P] + (iy - a.prow_r0[P]);
+            for (int t = a.prow_start[slot]; t < a.prow_start[slot + 1]; ++t) {
+                const int v = a.pedge_ids[t];
+                st += (unsigned long long)((a.verts[v].y > p.y) != (a.verts[a.nxt[v]].y > p.y));
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(FULL, e, o);
+        st += __shfl_xor_sync(FULL, st, o);
+    }
+    if (lane_id() == 0) {
+        atomicAdd(&out[0], e);
+        atomicAdd(&out[1], st);
+    }
+}
+
+cudaError_t launch_pip_census(const RefineArgs &a, const double2 *pts, int n, unsigned long long *out,
+                              cudaStream_t s) {
+    const int nb = std::max(1, std::min((n + 255) / 256, 152 * 16));
+    k_pip_census<<<nb, 256, 0, s>>>(a, pts, n, out);
+    return cudaGetLastError();
+}
+
 template <bool FP32>
 static size_t pip_smem_bytes() {
     return sizeof(PipSmem<FP32>) * PIP_WARPS;

@@ -71,3 +71,19 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(lib, walks):
         with pytest.raises(SJError) as e:
             api.p2p_join_noalloc(layer, p, torch.empty(10, dtype=torch.int32, device="cuda"), None)
         assert e.value.status == SJ_ERR_INVALID and "cells" in str(e.value)
+    # SJ_FP32X needs grid coordinates below 1e30 (its cell-relative FP32
+    # coordinates and rounding bounds assume them): refused as by sj_p2p_join
+    huge = dict(x0=0.0, y0=0.0, x1=4e30, y1=4e30, nx=4, ny=4)
+    hv = np.array([[1e30, 1e30]], np.float64)              # a one-vertex polyline: a point
+    with api.p2p_layer(hv, np.array([0, 1], np.int64), 100.0, huge) as layer:
+        p = torch.tensor([[1e30, 1e30]], dtype=torch.float64, device="cuda")
+        oid = torch.empty(1, dtype=torch.int32, device="cuda")
+        od = torch.empty(1, dtype=torch.float64, device="cuda")
+        for join in (lambda: api.p2p_join_noalloc(layer, p, oid, od, form="fp32x"),
+                     lambda: api.p2p_join(layer, p, oid, od, form="fp32x")):
+            with pytest.raises(SJError) as e:
+                join()
+            assert e.value.status == SJ_ERR_INVALID and "1e30" in str(e.value)
+        api.p2p_join_noalloc(layer, p, oid, od, form="fp64")
+        torch.cuda.synchronize()
+        assert int(oid[0]) == 0 and float(od[0]) == 0.0
