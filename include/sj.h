@@ -98,6 +98,16 @@ typedef struct {
 /* opts.flags: record CUDA events on the call's stream around the refinement
  * kernels; their summed elapsed time is reported by sj_layer_get_stats. */
 #define SJ_FLAG_TIME_REFINE 1
+/* opts.flags of the joins: order the points inside each grid cell by sub-cell
+ * (P2P: 4 x 4 sub-cells in Z-order; PIP: 8 horizontal bands) before they are
+ * cut into work items (SJ_FLAG_SUBCELL_ON), or keep them in arrival order
+ * (the default; SJ_FLAG_SUBCELL_OFF says so explicitly).  Results do not
+ * depend on it (a point's result depends on the point and the layer only).
+ * Work items of dense cells then cover compact parts of their cell, so the
+ * exact per-item prunes leave fewer tests, at the price of a per-sub-cell
+ * start table (4 bytes per sub-cell) in the bucketing. */
+#define SJ_FLAG_SUBCELL_ON 4
+#define SJ_FLAG_SUBCELL_OFF 8
 
 typedef struct sj_layer sj_layer;
 

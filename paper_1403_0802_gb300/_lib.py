@@ -63,6 +63,8 @@ SJ_FP64, SJ_FP32X = 0, 1
 SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
 SJ_FLAG_TIME_REFINE = 1
 SJ_FLAG_NO_GRAPH = 2
+SJ_FLAG_SUBCELL_ON = 4
+SJ_FLAG_SUBCELL_OFF = 8
 SJ_SERVE_BATCHED, SJ_SERVE_PER_REQUEST = 0, 1
 SJ_SERVE_PIP, SJ_SERVE_P2P = 0, 1
 

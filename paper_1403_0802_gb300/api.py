@@ -32,9 +32,11 @@ def _stream(stream) -> int | None:
     return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
 
 
-def _opts(form="fp64", launch="per_request", pts_per_item=0, time_refine=False) -> L.sj_opts:
-    return L.sj_opts(FORMS[form], LAUNCHES[launch], 0, int(pts_per_item), 0,
-                     L.SJ_FLAG_TIME_REFINE if time_refine else 0)
+def _opts(form="fp64", launch="per_request", pts_per_item=0, time_refine=False, subcell=None) -> L.sj_opts:
+    flags = L.SJ_FLAG_TIME_REFINE if time_refine else 0
+    if subcell is not None:
+        flags |= L.SJ_FLAG_SUBCELL_ON if subcell else L.SJ_FLAG_SUBCELL_OFF
+    return L.sj_opts(FORMS[form], LAUNCHES[launch], 0, int(pts_per_item), 0, flags)
 
 
 def _dev(a, dtype, device="cuda") -> torch.Tensor:
@@ -134,11 +136,13 @@ def _points(pts) -> torch.Tensor:
 
 
 def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp64", launch: str = "per_request",
-             pts_per_item: int = 0, stream=None, time_refine: bool = False) -> torch.Tensor:
-    """Polygon id (or -1) per point, int32 on the points' device (Sec. III.C)."""
+             pts_per_item: int = 0, stream=None, time_refine: bool = False, subcell: bool | None = None) -> torch.Tensor:
+    """Polygon id (or -1) per point, int32 on the points' device (Sec. III.C).
+    subcell: order points by sub-cell inside their cells (None: the library's
+    choice); results do not depend on it."""
     p = _points(pts)
     out = torch.empty(p.shape[0], dtype=torch.int32, device=p.device) if out is None else out
-    o = _opts(form, launch, pts_per_item, time_refine)
+    o = _opts(form, launch, pts_per_item, time_refine, subcell)
     L.check(L.lib().sj_pip_join(layer.handle, _ptr(p), p.shape[0], _ptr(out), C.byref(o), _stream(stream)),
             "sj_pip_join")
     return out
@@ -146,14 +150,14 @@ def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp
 
 def p2p_join(layer: Layer, pts, out_id: torch.Tensor | None = None, out_d: torch.Tensor | None = None,
              form: str = "fp64", launch: str = "per_request", pts_per_item: int = 0, stream=None,
-             time_refine: bool = False, window: float | None = None):
+             time_refine: bool = False, window: float | None = None, subcell: bool | None = None):
     """(nearest polyline id or -1, distance or +inf) per point (Sec. III.B); window (<= the layer's D)
-    replaces D for this call (sj_p2p_join_window)."""
+    replaces D for this call (sj_p2p_join_window); subcell as in pip_join."""
     p = _points(pts)
     n = p.shape[0]
     out_id = torch.empty(n, dtype=torch.int32, device=p.device) if out_id is None else out_id
     out_d = torch.empty(n, dtype=torch.float64, device=p.device) if out_d is None else out_d
-    o = _opts(form, launch, pts_per_item, time_refine)
+    o = _opts(form, launch, pts_per_item, time_refine, subcell)
     if window is None:
         L.check(L.lib().sj_p2p_join(layer.handle, _ptr(p), n, _ptr(out_id), _ptr(out_d), C.byref(o),
                                     _stream(stream)), "sj_p2p_join")

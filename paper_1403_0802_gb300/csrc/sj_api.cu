@@ -721,7 +721,7 @@ extern "C" sj_status sj_layer_reset_stats(sj_layer *L) {
 // ------------------------------------------------------------------ joins
 
 struct JoinBufs {
-    int *cnt, *cell_start, *perm, *totals, *pos, *res_id, *cell_base;
+    int *cnt, *cell_start, *perm, *totals, *pos, *res_id, *cell_base, *sub_start;
     int2 *key_rank, *items, *block_sums, *fb;
     double2 *spts;
     ResF *resf;
@@ -736,9 +736,10 @@ enum { RES_PERM = 0, RES_IDS, RES_F, RES_D };
 // with_spts: also a cell-ordered copy of the points (else the refinement reads
 // the input points through perm).
 static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb, bool with_spts = true,
-                  int res = RES_PERM) {
+                  int res = RES_PERM, int lS = 0) {
     size_t max_items = (size_t)(N / ch) + (size_t)std::min<int64_t>(G, N) + 1;
-    b.cnt = s.take<int>((size_t)G + 1);
+    b.cnt = s.take<int>(((size_t)G << lS) + 1);
+    b.sub_start = lS ? s.take<int>((size_t)G << lS) : nullptr;
     b.cell_start = s.take<int>((size_t)G + 1);
     b.totals = s.take<int>(4);
     b.key_rank = s.take<int2>((size_t)N);
@@ -786,14 +787,34 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     cudaStream_t s = (cudaStream_t)stream;
     const int G = L->g.G;
     const bool need_fb = (kind == KIND_P2P && form == SJ_FP32X);
+    // Sub-cell order of the points inside their cells (see BucketArgs), on
+    // request (SJ_FLAG_SUBCELL_ON): each work item of a dense cell then covers
+    // a compact part of it and the exact per-item prunes (the P2P box
+    // distance, the PIP y-range) drop more of the staged segments / edges --
+    // 40 % fewer P2P tests at 170 M points, 47 % fewer PIP tests on the
+    // heavy-tail tiling -- but the per-sub-cell start table (G x S entries,
+    // read at random by the scatter) costs more than that saves on the
+    // workloads measured, so arrival order is the default.  P2P: 4 x 4
+    // sub-cells in Z-order; PIP: 8 horizontal bands (its prune is in y).
+    int sub_lx = 0, sub_ly = 0;
+    {
+        const int fl = o ? o->flags : 0;
+        const bool on = (fl & SJ_FLAG_SUBCELL_ON) && !(fl & SJ_FLAG_SUBCELL_OFF);
+        if (on) {
+            if (kind == KIND_P2P) sub_lx = sub_ly = 2;
+            else sub_ly = 3;
+        }
+        if (((long long)G << (sub_lx + sub_ly)) > MAX_COUNT) sub_lx = sub_ly = 0;
+    }
+    const int lS = sub_lx + sub_ly;
 
     JoinBufs b;
     const int res = kind == KIND_PIP ? RES_IDS : (form == SJ_FP32X ? RES_F : RES_D);
-    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res); });
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res, lS); });
     Scratch sc;
     CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
-    carve(sc, b, N, G, ch, need_fb, false, res);
-    cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * ((size_t)G + 1), s);
+    carve(sc, b, N, G, ch, need_fb, false, res, lS);
+    cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * (((size_t)G << lS) + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
 
     BucketArgs ba{};
@@ -813,6 +834,9 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ba.totals = b.totals;
     ba.pos = b.pos;
     ba.cell_base = b.cell_base;
+    ba.sub_lx = sub_lx;
+    ba.sub_ly = sub_ly;
+    ba.sub_start = b.sub_start;
     if (e == cudaSuccess) e = launch_bucket(ba, s);
 
     RefineArgs ra{};

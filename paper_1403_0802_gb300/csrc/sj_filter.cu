@@ -171,9 +171,27 @@ constexpr int UNR = 4;
 // The step UNR * T can exceed the 2^22 headroom below 2^31 that the element
 // cap leaves, so the UNR kernels count in unsigned 32 bits: an index below
 // the cap plus a step below 2^31 stays below 2^32.
+// Counter of a point: its cell, or with sub-cell order the cell's sub-cell
+// (from FP32 estimates of the position inside the cell: any deterministic
+// choice is a valid order); the sentinel G (G * S) outside the grid.
+__device__ __forceinline__ int bucket_key(const BucketArgs &a, double x, double y) {
+    int ix, iy;
+    const int c = point_cell_xy(a.g, x, y, ix, iy);
+    if (a.sub_lx + a.sub_ly == 0) return c;
+    const int S = 1 << (a.sub_lx + a.sub_ly);
+    if (c >= a.g.G) return a.g.G * S;
+    const float fx = (approx_float(x) - a.g.x0f) * a.g.icwf - (float)ix;
+    const float fy = (approx_float(y) - a.g.y0f) * a.g.ichf - (float)iy;
+    const int nx = 1 << a.sub_lx, ny = 1 << a.sub_ly;
+    const int sx = min(max((int)(fx * (float)nx), 0), nx - 1);
+    const int sy = min(max((int)(fy * (float)ny), 0), ny - 1);
+    return c * S + sub_index(sx, sy, a.sub_lx, a.sub_ly);
+}
+
 __global__ void k_cell_hist(BucketArgs a) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     const unsigned T = gridDim.x * blockDim.x;
+    const int sentinel = a.g.G << (a.sub_lx + a.sub_ly);
     for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
         double2 p[UNR];
 #pragma unroll
@@ -185,11 +203,11 @@ __global__ void k_cell_hist(BucketArgs a) {
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const unsigned i = i0 + u * T;
-            c[u] = a.g.G;
+            c[u] = sentinel;
             r[u] = 0;
             if (i < (unsigned)a.n) {
-                c[u] = point_cell(a.g, p[u].x, p[u].y);
-                if (c[u] < a.g.G) r[u] = atomicAdd(&a.cnt[c[u]], 1);
+                c[u] = bucket_key(a, p[u].x, p[u].y);
+                if (c[u] < sentinel) r[u] = atomicAdd(&a.cnt[c[u]], 1);
             }
         }
 #pragma unroll
@@ -210,8 +228,15 @@ struct BucketLoad {
     const int *cnt;
     const int *cand_start;
     int ch;
+    int lS;           // log2 of the sub-cells per cell (0: none)
     __device__ int2 operator()(int c) const {
-        int np = cnt[c];
+        int np = 0;
+        if (lS == 0) {
+            np = cnt[c];
+        } else {
+            const int *q = cnt + ((size_t)c << lS);
+            for (int k = 0; k < (1 << lS); ++k) np += q[k];
+        }
         int ni = 0;
         if (cand_start && np > 0 && cand_start[c + 1] > cand_start[c]) ni = (np + ch - 1) / ch;
         return make_int2(np, ni);
@@ -222,12 +247,24 @@ struct BucketApply {
     int2 *items;
     int ch;
     int *cell_base;   // optional: cell_start of cells that yield items, else -1
+    const int *cnt;   // with sub-cells: their counters and first slots
+    int *sub_start;
+    int lS;
     __device__ void operator()(int c, int2 ex, int2 v, int n) const {
         cell_start[c] = ex.x;
         if (cell_base) cell_base[c] = v.y > 0 ? ex.x : -1;
         if (c == n - 1) cell_start[n] = ex.x + v.x;
         if (items)
             for (int t = 0; t < v.y; ++t) items[ex.y + t] = make_int2(c, t * ch);
+        if (lS > 0) {
+            const size_t b = (size_t)c << lS;
+            const bool none = cell_base && v.y == 0;
+            int run = ex.x;
+            for (int k = 0; k < (1 << lS); ++k) {
+                sub_start[b + k] = none ? -1 : run;
+                run += cnt[b + k];
+            }
+        }
     }
 };
 
@@ -239,7 +276,7 @@ __global__ void k_scatter(BucketArgs a) {
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const unsigned i = i0 + u * T;
-            k[u] = make_int2(a.g.G, 0);
+            k[u] = make_int2(a.g.G << (a.sub_lx + a.sub_ly), 0);
             if (i < (unsigned)a.n) {
                 k[u] = a.key_rank[i];
                 if (a.spts) p[u] = a.pts[i];
@@ -247,12 +284,16 @@ __global__ void k_scatter(BucketArgs a) {
         }
         // With a.pos (cell_base set): only points of cells that yield work
         // items get a slot; the others, like points outside the grid, get -1.
-        const int *base = a.pos ? a.cell_base : a.cell_start;
+        // With sub-cells the key is the sub-cell, whose first slot (or -1) is
+        // in sub_start.
+        const int lS = a.sub_lx + a.sub_ly;
+        const int *base = lS ? a.sub_start : (a.pos ? a.cell_base : a.cell_start);
+        const int sentinel = a.g.G << lS;
         int pos[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             pos[u] = -1;
-            if (k[u].x < a.g.G) {
+            if (k[u].x < sentinel) {
                 const int b = base[k[u].x];
                 pos[u] = b >= 0 ? b + k[u].y : -1;
             }
@@ -310,7 +351,9 @@ static int stream_blocks(long long n, int per_block, int cap) {
 // The scan alone (per-cell counts already in a.cnt): cell_start, work items
 // and totals.  Grid size depends only on G, so the launch can be replayed.
 cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
-    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch, a.cell_base}, a.g.G,
+    const int lS = a.sub_lx + a.sub_ly;
+    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch, lS},
+                    BucketApply{a.cell_start, a.items, a.ch, a.cell_base, a.cnt, a.sub_start, lS}, a.g.G,
                     a.block_sums, a.bs_cap, a.totals, s);
 }
 
@@ -359,9 +402,10 @@ cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s) {
     int nb = stream_blocks(a.n, 256, 152 * 32);
+    if (a.sub_lx < 0 || a.sub_ly < 0 || a.sub_lx > 3 || a.sub_ly > 3 || ((a.sub_lx + a.sub_ly) && !a.sub_start))
+        return cudaErrorInvalidValue;
     k_cell_hist<<<nb, 256, 0, s>>>(a);
-    cudaError_t e = run_scan(BucketLoad{a.cnt, a.cand_start, a.ch}, BucketApply{a.cell_start, a.items, a.ch, a.cell_base},
-                             a.g.G, a.block_sums, a.bs_cap, a.totals, s);
+    cudaError_t e = launch_bucket_scan(a, s);
     if (e != cudaSuccess) return e;
     k_scatter<<<nb, 256, 0, s>>>(a);
     return cudaGetLastError();

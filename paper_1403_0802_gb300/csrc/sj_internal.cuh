@@ -107,16 +107,21 @@ __device__ __forceinline__ int axis_cell(double v, const unsigned long long *key
 }
 
 // Cell id of a point (Sec. III.A), G when it lies outside the half-open grid
-// box or has a NaN or infinite coordinate.
-__device__ __forceinline__ int point_cell(const GridDev &g, double x, double y) {
+// box or has a NaN or infinite coordinate; (ix, iy) its column and row.
+__device__ __forceinline__ int point_cell_xy(const GridDev &g, double x, double y, int &ix, int &iy) {
     const unsigned long long EXP = 0x7ff0000000000000ULL;
+    ix = iy = -1;
     if (((unsigned long long)__double_as_longlong(x) & EXP) == EXP ||
         ((unsigned long long)__double_as_longlong(y) & EXP) == EXP)
         return g.G;
-    const int ix = axis_cell(x, g.kx, g.nx, g.x0f, g.icwf);
-    const int iy = axis_cell(y, g.ky, g.ny, g.y0f, g.ichf);
+    ix = axis_cell(x, g.kx, g.nx, g.x0f, g.icwf);
+    iy = axis_cell(y, g.ky, g.ny, g.y0f, g.ichf);
     if (ix < 0 || iy < 0) return g.G;
     return iy * g.nx + ix;
+}
+__device__ __forceinline__ int point_cell(const GridDev &g, double x, double y) {
+    int ix, iy;
+    return point_cell_xy(g, x, y, ix, iy);
 }
 
 // floor((v - lo) / w) clamped to [0, n - 1] (rasterisation of MBB corners).
@@ -136,6 +141,17 @@ __device__ __forceinline__ float2 cell_frame(const float *fx, const float *fy, i
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// 16-byte asynchronous copy global -> shared (cp.async, cached in L1); both
+// addresses 16-byte aligned.  The copying thread sees the data after
+// copy_async_wait_all().
+__device__ __forceinline__ void copy16_async(void *smem_dst, const void *gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void copy_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // Lanes per point group for a chunk of `nw` work units (edges / segments) and
 // `np` points: the power of two SG in {1..32} that minimises the number of
 // warp iterations ceil(np / (32 / SG)) * (ceil(nw / SG) + reduction steps).
@@ -143,10 +159,10 @@ __device__ __forceinline__ int choose_group(int np, int nw, int red_cost) {
     int best_sg = 1, best = 0x7fffffff;
 #pragma unroll
     for (int lg = 0; lg <= 5; ++lg) {
-        int sg = 1 << lg, pg = 32 >> lg;
-        int rounds = (np + pg - 1) / pg;
-        int cost = rounds * ((nw + sg - 1) / sg + lg * red_cost);
-        if (cost < best) { best = cost; best_sg = sg; }
+        // powers of two: shifts, not divisions
+        const int rounds = (np + (32 >> lg) - 1) >> (5 - lg);
+        const int cost = rounds * (((nw + (1 << lg) - 1) >> lg) + lg * red_cost);
+        if (cost < best) { best = cost; best_sg = 1 << lg; }
     }
     return best_sg;
 }
@@ -197,7 +213,7 @@ struct RefineArgs {
     const int *cseg_start;   // P2P: [G + 1] per-cell segment lists
     const int *cseg_ids;     //      segment (= first vertex) indices, ascending per cell
     const int *cell_algo;    //      [G] segments of the cell's candidate polylines
-    const float4 *cseg_rec;  //      [2 MS] FP32X staging records of the list entries (see sj_filter.cu)
+    const float4 *cseg_rec;  //      [2 MS] staging records of the list entries (see sj_filter.cu)
     const int *prow_base;    // PIP: [P + 1] first (polygon, row) slot of each polygon
     const int *prow_r0;      //      [P] first grid row of each polygon's MBB
     const int *prow_start;   //      [slots + 1] edge list range of each (polygon, row)
@@ -292,7 +308,27 @@ struct BucketArgs {
     int *pos;            // [n] sorted slot of each input point, -1 when its cell has no
                          //     candidates or it lies outside the grid (or null)
     int *cell_base;      // [G] with pos: cell_start of cells that yield work items, else -1
+    // Sub-cell order (sub_lx + sub_ly > 0): inside each cell the points are
+    // ordered by sub-cell, 2^sub_lx x 2^sub_ly sub-cells in Z-order, so that
+    // consecutive points of a cell -- one work item -- cover a compact part of
+    // it.  cnt then holds G * S + 1 counters (S = 2^(sub_lx + sub_ly)) and
+    // sub_start [G * S] the first slot of each sub-cell (-1 with pos for cells
+    // without work items).  The order is a pure permutation within cells: no
+    // result depends on it.
+    int sub_lx, sub_ly;
+    int *sub_start;
 };
+
+// Z-order index of sub-cell (sx, sy) with lx / ly bits per axis (at most 3).
+__device__ __forceinline__ int sub_index(int sx, int sy, int lx, int ly) {
+    int sub = 0, bit = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        if (b < lx) sub |= ((sx >> b) & 1) << bit++;
+        if (b < ly) sub |= ((sy >> b) & 1) << bit++;
+    }
+    return sub;
+}
 size_t bucket_scan_blocks(int G);
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s);
 // a8 for cell-ordered results: out[i] = res[pos[i]], or -1 / +inf where

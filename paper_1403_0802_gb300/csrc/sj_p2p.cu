@@ -57,11 +57,19 @@ struct alignas(16) Seg64 {
 template <bool FP32>
 struct P2PSmem;
 
+// FP32X staging holds segments in pairs (2k, 2k + 1), each quantity of the
+// pair side by side, so that one lane evaluates both with the packed FP32
+// instructions (FADD2 / FMUL2 / FFMA2: two IEEE round-to-nearest operations
+// each, the same roundings as the scalar ones).  The stored values are
+// negated (-a, -e, -1 / |e|^2), which keeps every packed operation an add or
+// a fused multiply-add of the stored operands; the arithmetic is the clamped
+// projection below, operation for operation.
 template <>
 struct P2PSmem<true> {
-    static constexpr int SMAX = 128;
-    float4 seg[SMAX];        // cell-relative a (x, y) and e (x, y)
-    float2 si[SMAX];         // (1 / |e|^2, polyline id as bits)
+    static constexpr int SMAX = 128;   // even
+    float4 sa[SMAX / 2];     // (-ax, -ax', -ay, -ay') cell-relative
+    float4 se[SMAX / 2];     // (-ex, -ex', -ey, -ey')
+    float4 si[SMAX / 2];     // (-1 / |e|^2, -1 / |e'|^2, polyline id bits, id' bits)
     float2 pt[MAX_CH];
     float b1[MAX_CH], b2[MAX_CH];
     int i1[MAX_CH];
@@ -78,14 +86,10 @@ struct P2PSmem<false> {
     int i1[MAX_CH];
 };
 
-// Squared distance from p to the segment (a, a + e) by the clamped projection.
-__device__ __forceinline__ float seg_d2(float px, float py, float ax, float ay, float ex, float ey, float inv) {
-    float dx = px - ax, dy = py - ay;
-    float t = __saturatef(fmaf(ex, dx, ey * dy) * inv);
-    float qx = fmaf(-t, ex, dx), qy = fmaf(-t, ey, dy);
-    return fmaf(qx, qx, qy * qy);
-}
-
+// Squared distance from p to the segment (a, a + e) by the clamped projection:
+// d = p - a, t = clamp((e . d) / |e|^2, 0, 1), |d - t e|^2, each operation
+// rounded once (FP64 here; the FP32X loop in p2p_compute evaluates the same
+// operations in FP32 on segment pairs).
 __device__ __forceinline__ double seg_d2(double px, double py, double ax, double ay, double ex, double ey,
                                          double inv) {
     double dx = __dsub_rn(px, ax), dy = __dsub_rn(py, ay);
@@ -167,7 +171,8 @@ __device__ __forceinline__ float key_float(int k) { return __int_as_float(k ^ ((
 __device__ __forceinline__ float warp_min(float v) { return key_float(__reduce_min_sync(FULL, float_key(v))); }
 __device__ __forceinline__ float warp_max(float v) { return key_float(__reduce_max_sync(FULL, float_key(v))); }
 
-// Refine the staged segments [0, ns) for the item's np points.  Rounds of 32
+// Refine the staged segments [0, ns) for the item's np points (FP32X: ns
+// counts segment pairs).  Rounds of 32
 // points take one lane per point (every lane busy, no merge); the last round,
 // of fewer than 32 points, splits each point's segments over a group of sg
 // lanes chosen by the cost model (more lanes per point, log2(sg) merges).
@@ -186,12 +191,26 @@ __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, in
         Best<T> st{INF, INF, -1};
         if (q < np) {
             if constexpr (FP32) {
+                // the squared distances of the pair by the clamped projection
+                // in FP32: dx = px - ax, t = sat(fma(ex, dx, ey * dy) / |e|^2),
+                // q = fma(-t, e, d), |q|^2 = fma(qx, qx, qy * qy), written with
+                // the negated operands (p + (-a) = p - a, fma(-ex, dx, -ey * dy)
+                // * (-1 / |e|^2) = (e . d) / |e|^2, fma(t, -e, d) = d - t e:
+                // each rounding the same as the unnegated one)
                 const float2 p = s.pt[q];
+                const float2 px = make_float2(p.x, p.x), py = make_float2(p.y, p.y);
 #pragma unroll 1
                 for (int t = sub; t < ns; t += sg) {
-                    const float4 g = s.seg[t];
-                    const float2 h = s.si[t];
-                    consider<true>(st, seg_d2(p.x, p.y, g.x, g.y, g.z, g.w, h.x), __float_as_int(h.y));
+                    const float4 A = s.sa[t], E = s.se[t], I = s.si[t];
+                    const float2 nex = make_float2(E.x, E.y), ney = make_float2(E.z, E.w);
+                    const float2 dx = __fadd2_rn(px, make_float2(A.x, A.y));
+                    const float2 dy = __fadd2_rn(py, make_float2(A.z, A.w));
+                    const float2 w = __ffma2_rn(nex, dx, __fmul2_rn(ney, dy));
+                    const float2 tt = make_float2(__saturatef(__fmul_rn(w.x, I.x)), __saturatef(__fmul_rn(w.y, I.y)));
+                    const float2 qx = __ffma2_rn(tt, nex, dx), qy = __ffma2_rn(tt, ney, dy);
+                    const float2 d = __ffma2_rn(qx, qx, __fmul2_rn(qy, qy));
+                    consider<true>(st, d.x, __float_as_int(I.z));
+                    consider<true>(st, d.y, __float_as_int(I.w));
                 }
             } else {
                 const double2 p = s.pt[q];
@@ -270,8 +289,33 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
 
         // 1. points: cell-relative FP32 coordinates, their box and magnitude
         float bxlo = FINF, bxhi = -FINF, bylo = FINF, byhi = -FINF;
+        // The (up to MAX_CH / 32) point loads of a lane are issued together --
+        // every slot index, then every point as an asynchronous copy into the
+        // (idle) staging area -- so that their latencies overlap instead of
+        // forming one chain per point.
+        constexpr int PQ = MAX_CH / 32;
+        double2 *pbuf;
+        if constexpr (FP32) {
+            static_assert(sizeof(P2PSmem<true>::sa) + sizeof(P2PSmem<true>::se) >= MAX_CH * sizeof(double2), "");
+            pbuf = reinterpret_cast<double2 *>(&s.sa[0]);   // sa and se, contiguous
+        } else {
+            static_assert(sizeof(P2PSmem<false>::seg) >= MAX_CH * sizeof(double2), "");
+            pbuf = reinterpret_cast<double2 *>(&s.seg[0]);
+        }
+        {
+            int src[PQ];
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                src[u] = q < np ? (a.spts ? j0 + q : a.perm[j0 + q]) : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < PQ; ++u)
+                if (src[u] >= 0) copy16_async(pbuf + lane + 32 * u, a.spts ? a.spts + src[u] : a.pts + src[u]);
+            copy_async_wait_all();
+        }
         for (int q = lane; q < np; q += 32) {
-            const double2 p = slot_point(a, j0 + q);
+            const double2 p = pbuf[q];
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
@@ -284,6 +328,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
             bxlo = fminf(bxlo, rx); bxhi = fmaxf(bxhi, rx);
             bylo = fminf(bylo, ry); byhi = fmaxf(byhi, ry);
         }
+        __syncwarp();   // every lane is done with the point buffer before staging reuses it
         bxlo = warp_min(bxlo); bylo = warp_min(bylo);
         bxhi = warp_max(bxhi); byhi = warp_max(byhi);
         // largest |coordinate| of the points: the larger magnitude of the box's ends
@@ -326,8 +371,13 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
             if (keep) {
                 const int pos = nst + __popc(bal & lt_mask);
                 if constexpr (FP32) {
-                    s.seg[pos] = make_float4(ax, ay, ex, ey);
-                    s.si[pos] = make_float2(inv, __int_as_float(sid));
+                    const int k = pos >> 1, h = pos & 1;
+                    float *A = reinterpret_cast<float *>(&s.sa[k]);
+                    float *E = reinterpret_cast<float *>(&s.se[k]);
+                    float *I = reinterpret_cast<float *>(&s.si[k]);
+                    A[h] = -ax; A[2 + h] = -ay;
+                    E[h] = -ex; E[2 + h] = -ey;
+                    I[h] = -inv; I[2 + h] = __int_as_float(sid);
                     mag = fmaxf(mag, smag);
                 } else {
                     const double2 v = a.verts[i], e = a.seg_e64[i];
@@ -338,9 +388,23 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
             }
             nst += __popc(bal);
             if (nst > SMAX - 32 || base + 32 >= g1) {
+                if constexpr (FP32) {
+                    // an odd count: the pair's second slot gets a segment at
+                    // infinite distance (a far point, zero length), which never
+                    // changes a point's top-2
+                    if ((nst & 1) && lane == 0) {
+                        const int k = nst >> 1;
+                        reinterpret_cast<float *>(&s.sa[k])[1] = -3.0e38f;
+                        reinterpret_cast<float *>(&s.sa[k])[3] = -3.0e38f;
+                        reinterpret_cast<float *>(&s.se[k])[1] = 0.0f;
+                        reinterpret_cast<float *>(&s.se[k])[3] = 0.0f;
+                        reinterpret_cast<float *>(&s.si[k])[1] = 0.0f;
+                        reinterpret_cast<float *>(&s.si[k])[3] = __int_as_float(-2);
+                    }
+                }
                 __syncwarp();
                 if (nst > 0) {
-                    p2p_compute<FP32>(s, np, nst, lane);
+                    p2p_compute<FP32>(s, np, FP32 ? (nst + 1) >> 1 : nst, lane);
                     c_tests += (unsigned long long)np * (unsigned long long)nst;
                 }
                 __syncwarp();

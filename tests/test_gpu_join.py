@@ -500,6 +500,43 @@ def test_host_join_pipelined_chunks(api, oracle, form):
                                       api.pip_join_host(layer, w.points, form=form))
 
 
+@pytest.mark.parametrize("form", FORMS)
+def test_subcell_order_gives_the_same_results(api, oracle, form):
+    """Points ordered by sub-cell inside their cells (SJ_FLAG_SUBCELL_ON) on
+    dense grids: P2P (2 M clustered points, 128 x 128 cells, 32 points per
+    work item: several items per cell) and PIP (the heavy-tail tiling, 1 M
+    points, 256 x 256 cells, 16 points per item) against the oracle, and
+    against arrival order within cells (FP64 bit for bit); the exact per-item
+    prunes then leave fewer tests."""
+    w = synth.p2p_walks(n_points=2_000_003, n_lines=20_000, grid_n=128)
+    Lw = w.polylines
+    ref = P2PRef(oracle, w.grid, Lw.verts, Lw.line_off, w.D)
+    r = ref.join(w.points)
+    res, tests = {}, {}
+    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+        pts = torch.as_tensor(w.points, device="cuda")
+        for sub in (False, True):
+            layer.reset_stats()
+            gid, gd = api.p2p_join(layer, pts, form=form, subcell=sub, pts_per_item=32)
+            res[sub] = (to_np(gid), to_np(gd))
+            tests[sub] = layer.stats()["edge_tests"]
+            ref.check(w.points, *res[sub], form, ref=r)
+    if form == "fp64":
+        np.testing.assert_array_equal(res[False][0], res[True][0])
+        np.testing.assert_array_equal(res[False][1], res[True][1])
+    assert tests[True] < 0.9 * tests[False]
+    w = synth.pip_tiles(n_points=1_000_003, layer=2, grid_n=256)
+    P = w.polygons
+    want = oracle.pip_join(w.grid, w.points, P.verts, P.ring_off, P.poly_ring_off)
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer:
+        for sub in (False, True):
+            layer.reset_stats()
+            got = to_np(api.pip_join(layer, w.points, form=form, subcell=sub, pts_per_item=16))
+            np.testing.assert_array_equal(got, want)
+            tests[sub] = layer.stats()["edge_tests"]
+    assert tests[True] < tests[False]
+
+
 def test_fp32x_fallback_rate_is_small(api, oracle):
     w = synth.p2p_walks(n_points=1_000_000)
     Lw = w.polylines
