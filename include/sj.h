@@ -139,6 +139,10 @@ typedef struct {
     int64_t census_tests;     /* sj_pip_census totals since the last reset: the  */
     int64_t census_straddles; /* edges of the points' candidate polygons, and how
                                  many of them straddle the point's y              */
+    int64_t resolved;         /* PIP: points whose cell's candidates are all
+                                 classified inside / outside, answered by the
+                                 cell-id pass without refinement (counted in
+                                 hits, not in items, pairs or algo_tests)         */
 } sj_run_stats;
 
 /* Build a resident polygon layer and its candidate lists (Sec. III.A: MBB of

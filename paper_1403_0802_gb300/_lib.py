@@ -34,7 +34,7 @@ class sj_run_stats(C.Structure):
     _fields_ = [("joins", C.c_int64), ("points", C.c_int64), ("items", C.c_int64), ("pairs", C.c_int64),
                 ("edge_tests", C.c_int64), ("fallbacks", C.c_int64), ("hits", C.c_int64),
                 ("refine_launches", C.c_int64), ("refine_ms", C.c_double), ("algo_tests", C.c_int64),
-                ("census_tests", C.c_int64), ("census_straddles", C.c_int64)]
+                ("census_tests", C.c_int64), ("census_straddles", C.c_int64), ("resolved", C.c_int64)]
 
 
 class sj_peak_rates(C.Structure):

@@ -169,6 +169,8 @@ void sj::fill_refine(const sj_layer *L, RefineArgs &ra) {
     ra.bnear_start = L->bnear_start;
     ra.bnear_ids = L->bnear_ids;
     ra.bnear_rec = L->bnear_rec;
+    ra.bnear_key = L->bnear_key;
+    ra.bnear_h = L->bnear_h;
     ra.bflip_start = L->bflip_start;
     ra.bflip_len = L->bflip_len;
     ra.bflip_keys = L->bflip_keys;
@@ -204,8 +206,8 @@ static void layer_free(sj_layer *L) {
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->prv, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
                     L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
-                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls, L->bnear_start, L->bnear_ids,
-                    L->bnear_rec, L->bflip_start, L->bflip_len, L->bflip_keys};
+                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls, L->cell_res, L->bnear_start, L->bnear_ids,
+                    L->bnear_rec, L->bnear_key, L->bnear_h, L->bflip_start, L->bflip_len, L->bflip_keys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     delete L;
@@ -374,10 +376,12 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     CUDA_TRY(dalloc(&L->bnear_start, (size_t)M + 1));
     CUDA_TRY(dalloc(&L->bflip_start, (size_t)M + 1));
     CUDA_TRY(dalloc(&L->bflip_len, (size_t)M));
+    CUDA_TRY(dalloc(&L->bnear_h, (size_t)M));
     if (M == 0) {
         L->MN = L->MF = 0;
         CUDA_TRY(dalloc(&L->bnear_ids, 0));
         CUDA_TRY(dalloc(&L->bnear_rec, 0));
+        CUDA_TRY(dalloc(&L->bnear_key, 0));
         CUDA_TRY(dalloc(&L->bflip_keys, 0));
         CUDA_TRY(cudaMemsetAsync(L->bnear_start, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(L->bflip_start, 0, sizeof(int), s));
@@ -432,6 +436,7 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     L->MF = tot[4];
     CUDA_TRY(dalloc(&L->bnear_ids, (size_t)L->MN));
     CUDA_TRY(dalloc(&L->bnear_rec, 2 * (size_t)L->MN));
+    CUDA_TRY(dalloc(&L->bnear_key, (size_t)L->MN));
     CUDA_TRY(dalloc(&L->bflip_keys, (size_t)L->MF));
     a.near_start = L->bnear_start;
     a.flip_start = L->bflip_start;
@@ -439,6 +444,9 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     a.flip_keys = L->bflip_keys;
     CUDA_TRY(launch_pip_boundary(a, 1, s));
     CUDA_TRY(launch_pip_flips(L->bflip_start, M, L->bflip_keys, L->bflip_len, s));
+    // near lists ordered by lower y, with their keys and y-extents (the
+    // refinement's window search on long lists), then the staging records
+    CUDA_TRY(launch_pip_near_sort(L->bnear_start, M, L->bnear_ids, L->nxt, L->vsplit, L->bnear_key, L->bnear_h, s));
     if (L->MN > 0) CUDA_TRY(launch_prow_records(L->bnear_ids, (long long)L->MN, L->nxt, L->vsplit, L->bnear_rec, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
@@ -455,6 +463,8 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
         CUDA_TRY(dalloc(&L->pedge_ids, 0));
         CUDA_TRY(dalloc(&L->pedge_rec, 0));
         CUDA_TRY(dalloc(&L->cand_cls, 0));
+        CUDA_TRY(dalloc(&L->cell_res, (size_t)L->g.G));
+        CUDA_TRY(cudaMemsetAsync(L->cell_res, 0xff, sizeof(int) * (size_t)L->g.G, s));   // -1: no candidates
         CUDA_TRY(cudaMemsetAsync(L->prow_base, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(L->prow_start, 0, sizeof(int), s));
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -521,6 +531,9 @@ static sj_status build_row_lists(sj_layer *L, cudaStream_t s) {
     if (L->M > 0)
         CUDA_TRY(launch_pip_classify(L->g, L->cand_start, L->cand_ids, L->prow_base, L->prow_r0, L->prow_start,
                                      L->pedge_ids, L->nxt, L->verts, delta, L->cand_cls, s));
+    // per cell: the result of its points when every candidate is classified
+    CUDA_TRY(dalloc(&L->cell_res, (size_t)L->g.G));
+    CUDA_TRY(launch_cell_result(L->cand_start, L->cand_ids, L->cand_cls, L->g.G, L->cell_res, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return build_boundary_lists(L, delta, s);
 }
@@ -699,6 +712,7 @@ extern "C" sj_status sj_layer_get_stats(const sj_layer *L, sj_run_stats *out) {
     out->fallbacks = (int64_t)h[ST_FALLBACK];
     out->hits = (int64_t)h[ST_HITS];
     out->algo_tests = (int64_t)h[ST_ALGO];
+    out->resolved = (int64_t)h[ST_RESOLVED];
     out->census_tests = L->census_tests.load();
     out->census_straddles = L->census_straddles.load();
     return SJ_OK;
@@ -837,6 +851,11 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ba.sub_lx = sub_lx;
     ba.sub_ly = sub_ly;
     ba.sub_start = b.sub_start;
+    if (kind == KIND_PIP) {   // points of fully classified cells: results written by the cell-id pass
+        ba.cell_res = L->cell_res;
+        ba.out_id = out_id;
+        ba.stats = L->stats;
+    }
     if (e == cudaSuccess) e = launch_bucket(ba, s);
 
     RefineArgs ra{};

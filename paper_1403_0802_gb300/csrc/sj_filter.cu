@@ -191,7 +191,9 @@ __device__ __forceinline__ int bucket_key(const BucketArgs &a, double x, double 
 __global__ void k_cell_hist(BucketArgs a) {
     const double inf = __longlong_as_double(0x7ff0000000000000LL);
     const unsigned T = gridDim.x * blockDim.x;
-    const int sentinel = a.g.G << (a.sub_lx + a.sub_ly);
+    const int lS = a.sub_lx + a.sub_ly;
+    const int sentinel = a.g.G << lS;
+    unsigned resolved = 0, rhits = 0;
     for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
         double2 p[UNR];
 #pragma unroll
@@ -199,14 +201,24 @@ __global__ void k_cell_hist(BucketArgs a) {
             const unsigned i = i0 + u * T;
             if (i < (unsigned)a.n) p[u] = a.pts[i];
         }
-        int c[UNR], r[UNR];
+        // key (sentinel outside the grid), rank in its counter; a point of a
+        // cell whose result is known (cell_res) gets key sentinel, rank 1
+        int c[UNR], r[UNR], v[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const unsigned i = i0 + u * T;
             c[u] = sentinel;
             r[u] = 0;
+            v[u] = CELL_REFINE;
             if (i < (unsigned)a.n) {
                 c[u] = bucket_key(a, p[u].x, p[u].y);
+                if (a.cell_res && c[u] < sentinel) {
+                    v[u] = a.cell_res[c[u] >> lS];
+                    if (v[u] != CELL_REFINE) {
+                        c[u] = sentinel;
+                        r[u] = 1;
+                    }
+                }
                 if (c[u] < sentinel) r[u] = atomicAdd(&a.cnt[c[u]], 1);
             }
         }
@@ -215,10 +227,24 @@ __global__ void k_cell_hist(BucketArgs a) {
             const unsigned i = i0 + u * T;
             if (i < (unsigned)a.n) {
                 a.key_rank[i] = make_int2(c[u], r[u]);
-                if (a.out_id) a.out_id[i] = -1;
-                if (a.out_d) a.out_d[i] = inf;
+                if (a.cell_res) {
+                    if (v[u] != CELL_REFINE) {
+                        a.out_id[i] = v[u];
+                        ++resolved;
+                        rhits += v[u] >= 0;
+                    }
+                } else {
+                    if (a.out_id) a.out_id[i] = -1;
+                    if (a.out_d) a.out_d[i] = inf;
+                }
             }
         }
+    }
+    if (a.stats) {
+        unsigned long long v[ST_N] = {};
+        v[ST_RESOLVED] = __reduce_add_sync(FULL, resolved);
+        v[ST_HITS] = __reduce_add_sync(FULL, rhits);
+        flush_stats(a.stats, v);
     }
 }
 
@@ -292,7 +318,7 @@ __global__ void k_scatter(BucketArgs a) {
         int pos[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            pos[u] = -1;
+            pos[u] = (k[u].x >= sentinel && k[u].y == 1) ? POS_DONE : -1;   // result already written, or outside
             if (k[u].x < sentinel) {
                 const int b = base[k[u].x];
                 pos[u] = b >= 0 ? b + k[u].y : -1;
@@ -333,7 +359,7 @@ __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d,
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const unsigned i = i0 + u * T;
-            if (i < (unsigned)n) {
+            if (i < (unsigned)n && j[u] != POS_DONE) {
                 out_id[i] = id[u];
                 if (out_d) out_d[i] = d[u];
             }

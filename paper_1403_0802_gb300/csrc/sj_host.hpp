@@ -56,12 +56,15 @@ struct sj_layer {
     int *pedge_ids = nullptr;    // [ME] edge (= first vertex) indices
     float4 *pedge_rec = nullptr; // [2 ME] FP32X staging records: vsplit of the edge's two ends
     unsigned char *cand_cls = nullptr;   // [M] per candidate entry: 0 boundary, 1 inside, 2 outside
+    int *cell_res = nullptr;             // [G] result of every point of a fully classified cell, or CELL_REFINE
     // PIP boundary entries (class 0): near edges (x-range meets the cell's column
     // widened by delta) and the flip keys of the far-right edges' parity in y
     int64_t MN = 0, MF = 0;
     int *bnear_start = nullptr;              // [M + 1]
     int *bnear_ids = nullptr;                // [MN]
     float4 *bnear_rec = nullptr;             // [2 MN] vsplit of both ends
+    float *bnear_key = nullptr;              // [MN] lower truncated y of each near edge, ascending per entry
+    float *bnear_h = nullptr;                // [M] largest truncated y-extent of an entry's near edges
     int *bflip_start = nullptr;              // [M + 1]
     int *bflip_len = nullptr;                // [M] keys left after cancelling equal pairs
     unsigned long long *bflip_keys = nullptr;   // [MF] order keys, ascending within an entry

@@ -176,7 +176,26 @@ struct Box {
 enum { KIND_PIP = 0, KIND_P2P = 1 };
 
 // Per-layer device counters (index into sj_run_stats order after `joins`).
-enum { ST_POINTS = 0, ST_ITEMS, ST_PAIRS, ST_TESTS, ST_FALLBACK, ST_HITS, ST_ALGO, ST_N };
+enum { ST_POINTS = 0, ST_ITEMS, ST_PAIRS, ST_TESTS, ST_FALLBACK, ST_HITS, ST_ALGO, ST_RESOLVED, ST_N };
+
+// cell_res value of a polygon-layer cell whose points need the refinement.
+constexpr int CELL_REFINE = -2;
+
+// Adds counters to the layer's statistics with one global atomic per counter
+// and block: every lane 0 of the block's warps passes its warp's values
+// (others pass zeros), the block sums them in shared memory first.  Every
+// thread of the block must call it (it synchronises the block).  Thousands of
+// warps adding to the same few addresses would otherwise queue at the L2.
+__device__ __forceinline__ void flush_stats(unsigned long long *stats, const unsigned long long *v) {
+    __shared__ unsigned long long blk[ST_N];
+    if (threadIdx.x < ST_N) blk[threadIdx.x] = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0)
+        for (int k = 0; k < ST_N; ++k)
+            if (v[k]) atomicAdd(&blk[k], v[k]);
+    __syncthreads();
+    if (threadIdx.x < ST_N && blk[threadIdx.x]) atomicAdd(&stats[threadIdx.x], blk[threadIdx.x]);
+}
 
 // Cell-ordered P2P results of a per-request join, one record per slot so that
 // the final gather to input order reads one place per point.
@@ -224,6 +243,8 @@ struct RefineArgs {
     const int *bnear_start;  // PIP boundary entries: near edge lists [M + 1]
     const int *bnear_ids;
     const float4 *bnear_rec; //      [2 per edge] vsplit of both ends
+    const float *bnear_key;  //      per near edge: min of its ends' FP32 truncated y (ascending per entry)
+    const float *bnear_h;    //      [M] largest (max - min) truncated y of an entry's edges, rounded up
     const int *bflip_start;  //      far-right parity flips: [M + 1] starts,
     const int *bflip_len;    //      [M] lengths,
     const unsigned long long *bflip_keys;   // ascending order keys of the flip y-values
@@ -275,8 +296,12 @@ struct BoundaryArgs {
 };
 cudaError_t launch_pip_boundary(const BoundaryArgs &a, int emit, cudaStream_t s);
 cudaError_t launch_pip_flips(const int *flip_start, int M, unsigned long long *keys, int *len, cudaStream_t s);
+cudaError_t launch_pip_near_sort(const int *near_start, int M, int *ids, const int *nxt, const float4 *vsplit,
+                                 float *keys, float *h, cudaStream_t s);
 
 // PIP cell classification (layer build): one class per candidate entry.
+cudaError_t launch_cell_result(const int *cand_start, const int *cand_ids, const unsigned char *cls, int G, int *res,
+                               cudaStream_t s);
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
                                 const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
                                 const double2 *verts, double delta, unsigned char *cls, cudaStream_t s);
@@ -317,7 +342,14 @@ struct BucketArgs {
     // result depends on it.
     int sub_lx, sub_ly;
     int *sub_start;
+    // PIP: per cell the result of every point of a cell whose candidates are
+    // all classified inside / outside, else CELL_REFINE (or null).  Such a
+    // point's result is written to out_id by the cell-id pass itself; it gets
+    // no slot (pos = POS_DONE) and no work item.
+    const int *cell_res;
+    unsigned long long *stats;   // ST_RESOLVED counts those points (or null)
 };
+constexpr int POS_DONE = -2;   // pos of a point whose result the cell-id pass wrote
 
 // Z-order index of sub-cell (sx, sy) with lx / ly bits per axis (at most 3).
 __device__ __forceinline__ int sub_index(int sx, int sy, int lx, int ly) {

@@ -473,16 +473,14 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
         cs1 = cs1n;
     }
     if (a.stats) {
-        c_fb = __reduce_add_sync(FULL, c_fb);
-        c_hits = __reduce_add_sync(FULL, c_hits);
-        if (lane == 0) {
-            atomicAdd(&a.stats[ST_ITEMS], c_items);
-            atomicAdd(&a.stats[ST_PAIRS], c_pairs);
-            atomicAdd(&a.stats[ST_TESTS], c_tests);
-            atomicAdd(&a.stats[ST_ALGO], c_algo);
-            atomicAdd(&a.stats[ST_FALLBACK], (unsigned long long)c_fb);
-            atomicAdd(&a.stats[ST_HITS], (unsigned long long)c_hits);
-        }
+        unsigned long long v[ST_N] = {};
+        v[ST_ITEMS] = c_items;
+        v[ST_PAIRS] = c_pairs;
+        v[ST_TESTS] = c_tests;
+        v[ST_ALGO] = c_algo;
+        v[ST_FALLBACK] = __reduce_add_sync(FULL, c_fb);
+        v[ST_HITS] = __reduce_add_sync(FULL, c_hits);
+        flush_stats(a.stats, v);
     }
 }
 

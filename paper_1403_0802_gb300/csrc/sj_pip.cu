@@ -126,6 +126,55 @@ __device__ __forceinline__ bool orient32(float px, float py, float lx, float ly,
     return fabsf(d) > E;
 }
 
+// Near lists longer than this are not staged: each pending point searches
+// the window of the sorted list that can hold its straddling edges.
+constexpr int LONG_NEAR = 128;
+
+// Crossing of near edge e (boundary list entry) for point q of the item, the
+// arithmetic of pip_compute for one edge: FP32X on the edge's staging record
+// (FP32 straddle test on truncations, certified orientation, FP64 rule on a
+// tie or an uncertain sign), FP64 on the original vertices.
+template <bool FP32>
+__device__ __forceinline__ int near_edge_cross(const RefineArgs &a, const PipSmem<FP32> &s, int q, int e, float2 fo,
+                                               unsigned &c_fb) {
+    if constexpr (FP32) {
+        const float pyh = s.pyh[q];
+        const float4 va = a.bnear_rec[2 * (size_t)e], vc = a.bnear_rec[2 * (size_t)e + 1];
+        if ((va.y == pyh) | (vc.y == pyh)) {   // FP32 y tie: decide in FP64
+            ++c_fb;
+            return cross64_global(a, a.bnear_ids[e], s.pin[q]);
+        }
+        const bool a_up = va.y > pyh, b_up = vc.y > pyh;
+        if (a_up == b_up) return 0;
+        const float ax = rel_coord(va.x, va.z, fo.x), ay = rel_coord(va.y, va.w, fo.y);
+        const float bx = rel_coord(vc.x, vc.z, fo.x), by = rel_coord(vc.y, vc.w, fo.y);
+        const float lx = a_up ? bx : ax, ly = a_up ? by : ay;
+        const float hx = a_up ? ax : bx, hy = a_up ? ay : by;
+        const float2 p = s.pt[q];
+        bool pos;
+        if (orient32(p.x, p.y, lx, ly, hx, hy, a.eps_abs, pos)) return (int)pos;
+        ++c_fb;
+        return cross64_global(a, a.bnear_ids[e], s.pin[q]);
+    } else {
+        const int i = a.bnear_ids[e];
+        const double2 A = a.verts[i], B = a.verts[a.nxt[i]], p = s.pt[q];
+        return cross64(p.x, p.y, A.x, A.y, B.x, B.y);
+    }
+}
+
+// First index t in [0, n) with keys[t] >= x (upper = false) or > x (upper =
+// true), n if none.
+__device__ __forceinline__ int key_bound(const float *keys, int n, float x, bool upper) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const float k = keys[mid];
+        if (upper ? (k <= x) : (k < x)) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Parity masks of the staged edges [0, ns) for the item's pending points.
 template <bool FP32>
 __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, const RefineArgs &a, int j0, int np,
@@ -193,7 +242,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
     const int n_items = *a.n_items;
     const float FINF = __int_as_float(0x7f800000);
     const unsigned lt_mask = (1u << lane) - 1u;
-    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0;
+    unsigned long long c_pairs = 0, c_tests = 0, c_items = 0, c_algo = 0, c_wtests = 0;
     unsigned c_fb = 0, c_hits = 0;
 
     // Items come from a device counter when a.work_next is set (the next index
@@ -297,6 +346,30 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
                     if (lo & 1) s.par[q] ^= 1u << j;
                 }
             }
+            // long near lists: each pending point tests only the edges whose
+            // lower truncated y lies in [fl_down(y - h), y] (two binary
+            // searches in the sorted list); no other edge of the list can
+            // straddle its y (nor tie with it), so the parity is unchanged
+            const bool lng = ne > LONG_NEAR;
+            for (unsigned lm = __ballot_sync(FULL, lng); lm; lm &= lm - 1) {
+                const int j = __ffs(lm) - 1;
+                const int b0 = __shfl_sync(FULL, vb, j), n0 = __shfl_sync(FULL, ne, j);
+                const float hj = a.bnear_h[kg + j];
+                const float *keys = a.bnear_key + b0;
+                for (int q = lane; q < np; q += 32) {
+                    if (s.found[q] >= 0) continue;
+                    float pyh;
+                    if constexpr (FP32) pyh = s.pyh[q];
+                    else pyh = approx_float(s.pt[q].y);
+                    const int lo = key_bound(keys, n0, __fsub_rd(pyh, hj), false);
+                    const int hi = key_bound(keys, n0, pyh, true);
+                    unsigned par = 0;
+                    for (int t = lo; t < hi; ++t) par ^= (unsigned)near_edge_cross<FP32>(a, s, q, b0 + t, fo, c_fb);
+                    c_wtests += (unsigned long long)(hi > lo ? hi - lo : 0);
+                    if (par & 1u) s.par[q] ^= 1u << j;
+                }
+            }
+            if (lng) ne = 0;   // staged below: the short lists only
             __syncwarp();
             c_pairs += (unsigned long long)pending * (unsigned long long)nc;
             c_algo += (unsigned long long)pending * (unsigned long long)__reduce_add_sync(FULL, (unsigned)nall);
@@ -391,15 +464,16 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
     if (a.stats) {
         c_fb = __reduce_add_sync(FULL, c_fb);
         c_hits = __reduce_add_sync(FULL, c_hits);
-        const unsigned long long t = c_tests;   // per lane: tests of the rounds it led
-        if (lane == 0) {
-            atomicAdd(&a.stats[ST_ITEMS], c_items);
-            atomicAdd(&a.stats[ST_PAIRS], c_pairs);
-            atomicAdd(&a.stats[ST_TESTS], t);
-            atomicAdd(&a.stats[ST_ALGO], c_algo);
-            atomicAdd(&a.stats[ST_FALLBACK], (unsigned long long)c_fb);
-            atomicAdd(&a.stats[ST_HITS], (unsigned long long)c_hits);
-        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c_wtests += __shfl_xor_sync(FULL, c_wtests, o);
+        unsigned long long v[ST_N] = {};
+        v[ST_ITEMS] = c_items;
+        v[ST_PAIRS] = c_pairs;
+        v[ST_TESTS] = c_tests + c_wtests;   // staged tests (warp-uniform) + window tests
+        v[ST_ALGO] = c_algo;
+        v[ST_FALLBACK] = c_fb;
+        v[ST_HITS] = c_hits;
+        flush_stats(a.stats, v);
     }
 }
 
@@ -447,6 +521,32 @@ __global__ void k_pip_classify(GridDev g, const int *cand_start, const int *cand
             if (lane == 0) cls[k] = hit ? 0 : (par ? 1 : 2);
         }
     }
+}
+
+// Per cell of a polygon layer: the result every point of the cell gets when
+// each of its candidates is classified (class 1 inside or 2 outside) -- the
+// smallest candidate whose class is inside (candidate ids are sorted), or -1
+// -- else CELL_REFINE: some candidate is a boundary candidate and the cell's
+// points go through the refinement.  Cells without candidates get -1.
+__global__ void k_cell_result(const int *cand_start, const int *cand_ids, const unsigned char *cls, int G, int *res) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
+        int r = -1;
+        for (int k = cand_start[c]; k < cand_start[c + 1]; ++k) {
+            if (cls[k] == 0) {
+                r = CELL_REFINE;
+                break;
+            }
+            if (cls[k] == 1 && r == -1) r = cand_ids[k];
+        }
+        res[c] = r;
+    }
+}
+
+cudaError_t launch_cell_result(const int *cand_start, const int *cand_ids, const unsigned char *cls, int G, int *res,
+                               cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>(((long long)G + 255) / 256, 152LL * 32));
+    k_cell_result<<<nb, 256, 0, s>>>(cand_start, cand_ids, cls, G, res);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
@@ -573,6 +673,60 @@ __global__ void k_pip_flips(const int *flip_start, int M, unsigned long long *ke
         }
         len[k] = m;
     }
+}
+
+// Near lists sorted by lower y (layer build), one thread per boundary entry:
+// key = min(trunc32(a.y), trunc32(b.y)) of each near edge (the FP32 truncations
+// the refinement compares, a monotone map of y), ids reordered by key (Shell
+// sort, Ciura gaps), and h[k] = the largest max - min of the two truncations
+// over the entry's edges, rounded up.  An edge of the list can straddle (or
+// tie with) a point's truncated y only if its key lies in
+// [fl_down(y - h), y]: the refinement finds that window by binary search.
+__global__ void k_pip_near_sort(const int *near_start, int M, int *ids, const int *nxt, const float4 *vsplit,
+                                float *keys, float *h) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < M; k += gridDim.x * blockDim.x) {
+        const int b = near_start[k], n = near_start[k + 1] - b;
+        float hk = 0.0f;
+        for (int t = 0; t < n; ++t) {
+            const int i = ids[b + t];
+            const float ya = vsplit[i].y, yb = vsplit[nxt[i]].y;
+            keys[b + t] = fminf(ya, yb);
+            hk = fmaxf(hk, __fsub_ru(fmaxf(ya, yb), fminf(ya, yb)));
+        }
+        h[k] = hk;
+        const int ciura[8] = {1, 4, 10, 23, 57, 132, 301, 701};
+        int gaps[32];
+        int ng = 0;
+        while (ng < 8 && ciura[ng] < n) { gaps[ng] = ciura[ng]; ++ng; }
+        if (ng == 8) {
+            long long g = 701;
+            while (ng < 32 && (g = g * 9 / 4) < n) gaps[ng++] = (int)g;
+        }
+        float *kv = keys + b;
+        int *iv = ids + b;
+        for (int u = ng - 1; u >= 0; --u) {
+            const int gp = gaps[u];
+            for (int i = gp; i < n; ++i) {
+                const float x = kv[i];
+                const int xi = iv[i];
+                int j = i;
+                while (j >= gp && kv[j - gp] > x) {
+                    kv[j] = kv[j - gp];
+                    iv[j] = iv[j - gp];
+                    j -= gp;
+                }
+                kv[j] = x;
+                iv[j] = xi;
+            }
+        }
+    }
+}
+
+cudaError_t launch_pip_near_sort(const int *near_start, int M, int *ids, const int *nxt, const float4 *vsplit,
+                                 float *keys, float *h, cudaStream_t s) {
+    const int nb = std::max(1, std::min((M + 127) / 128, 8192));
+    k_pip_near_sort<<<nb, 128, 0, s>>>(near_start, M, ids, nxt, vsplit, keys, h);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pip_boundary(const BoundaryArgs &a, int emit, cudaStream_t s) {

@@ -77,7 +77,7 @@ def test_struct_layouts_match_header():
     from paper_1403_0802_gb300 import _lib
     assert C.sizeof(_lib.sj_grid) == 40
     assert C.sizeof(_lib.sj_opts) == 24
-    assert C.sizeof(_lib.sj_run_stats) == 96
+    assert C.sizeof(_lib.sj_run_stats) == 104
     assert C.sizeof(_lib.sj_layer_info) == 48
 
 

@@ -109,6 +109,7 @@ def test_pip_stars_full_size(api, oracle, form):
         st = layer.stats()
     np.testing.assert_array_equal(got, ref)
     assert st["hits"] == (ref >= 0).sum()
+    assert 0 < st["resolved"] < len(ref)           # classified cells answered without refinement
 
 
 @pytest.mark.parametrize("form", FORMS)
@@ -163,6 +164,36 @@ def test_pip_degenerate_integer_tiling(api, oracle, form):
     np.testing.assert_array_equal(got, ref)
     if form == "fp32x":
         assert st["fallbacks"] > 0
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pip_long_near_lists_window_search(api, oracle, form):
+    """A polygon whose right side is a 2,048-vertex zigzag inside one grid
+    column: every cell of that column has a near list of ~256 edges (longer
+    than the refinement stages), searched per point in its sorted window.
+    Points on the zigzag's vertices and edge midpoints, at the vertices' exact
+    y values (FP32 ties) and uniform points: ids bit-identical to the oracle,
+    with far fewer tests than points x list length."""
+    n, W, A, H = 2048, 32.0, 7.0, 64.0
+    ys = np.arange(n + 1) * (H / n)                          # dyadic steps of 1/32
+    xs = W + A * (np.arange(n + 1) % 2)
+    ring = np.concatenate([[[0.0, 0.0]], np.stack([xs, ys], 1), [[0.0, H]]])
+    verts = np.ascontiguousarray(ring, np.float64)
+    ring_off = np.array([0, len(verts)], np.int64)
+    poly_off = np.array([0, 1], np.int64)
+    g = dict(x0=0.0, y0=0.0, x1=128.0, y1=128.0, nx=16, ny=16)
+    rng = np.random.default_rng(11)
+    mids = 0.5 * (verts[1:n + 1] + verts[2:n + 2])
+    tie = np.stack([rng.uniform(W, W + A, n + 1), ys], 1)
+    pts = np.concatenate([rng.uniform(0, 128, (60_000, 2)), verts, mids, tie,
+                          np.stack([np.full(n + 1, W + 0.5 * A), ys], 1)])
+    ref = oracle.pip_join(g, pts, verts, ring_off, poly_off)
+    assert 0 < (ref == 0).sum() < len(pts)
+    with api.pip_layer(verts, ring_off, poly_off, g) as layer:
+        got = to_np(api.pip_join(layer, pts, form=form))
+        st = layer.stats()
+    np.testing.assert_array_equal(got, ref)
+    assert st["edge_tests"] < 0.1 * (st["points"] - st["resolved"]) * 256
 
 
 @pytest.mark.parametrize("form", FORMS)
