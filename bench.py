@@ -108,13 +108,25 @@ def workload(args, rank: int = 0):
     raise ValueError(args.workload)
 
 
-def default_ppi(args) -> int:
-    """Points per work item: --ppi, else the autotuner's best for the workload
-    at its full size (128, the library default, except 64 on the heavy-tail
-    tiling, whose boundary cells stage long near-edge lists per item)."""
+# Launch settings per workload at full size: the fastest row of
+# paper_1403_0802_gb300.autotune on GB300 (points per item x warps per block x
+# edges per chunk; 0 = the library default).
+TUNED = {"p2p": dict(ppi=128, block=4, edges=0), "pip": dict(ppi=128, block=4, edges=0),
+         "pip3_1": dict(ppi=128, block=8, edges=64), "pip3_2": dict(ppi=128, block=2, edges=64),
+         "pip3_3": dict(ppi=128, block=8, edges=64), "p2p4": dict(ppi=128, block=4, edges=0)}
+
+
+def tuned(args) -> dict:
+    key = f"pip3_{args.layer}" if args.workload == "pip3" else args.workload
+    t = dict(TUNED.get(key, dict(ppi=0, block=0, edges=0)))
     if args.ppi:
-        return args.ppi
-    return 64 if (args.workload == "pip3" and args.layer == 2) else 0
+        t["ppi"] = args.ppi
+    return t
+
+
+def default_ppi(args) -> int:
+    """Points per work item: --ppi, else the autotuned setting."""
+    return tuned(args)["ppi"]
 
 
 def dist_env():
@@ -309,8 +321,10 @@ def metric_name(kind):
 
 
 def config_of(w, args):
+    t = tuned(args)
     c = {"workload": w.name, "points": int(len(w.points)), "grid": f"{w.grid['nx']}x{w.grid['ny']}",
-         "form": args.form, "launch": "per_request", "pts_per_item": default_ppi(args) or 128}
+         "form": args.form, "launch": "per_request", "pts_per_item": t["ppi"] or 128,
+         "warps_per_block": t["block"] or 4, "edges_per_chunk": t["edges"] or ("64" if w.kind == "pip" else "none")}
     big = len(w.points) * 16 > 129e6
     c["l2"] = ("inputs larger than L2 (points %d MB > 129 MB); no flush" % (len(w.points) * 16 // 10 ** 6) if big
                else "points %d MB fit in L2; steps re-read them (no flush)" % (len(w.points) * 16 // 10 ** 6))
@@ -385,7 +399,8 @@ def run_reference(args):
         "e2e": {"value": v, "unit": "points/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=True, ppi=0, clk=None, outs=None):
+def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=True, ppi=0, clk=None, outs=None,
+               knobs=None):
     """Mean CUDA-event time over `steps` joins after `warmup` untimed ones (the
     layer's counters cover the timed joins only); returns (total ms, stats,
     (out_id, out_d))."""
@@ -395,12 +410,15 @@ def time_joins(api, layer, w, pts, form, steps, warmup, world, stream, timed=Tru
     out_d = (torch.empty(n, dtype=torch.float64, device=pts.device) if outs is None else outs[1]) \
         if w.kind == "p2p" else None
 
+    kn = knobs or {}
+
     def one(time_refine):
         if w.kind == "p2p":
             api.p2p_join(layer, pts, out_id, out_d, form=form, stream=stream, time_refine=time_refine,
-                         pts_per_item=ppi)
+                         pts_per_item=ppi, **kn)
         else:
-            api.pip_join(layer, pts, out_id, form=form, stream=stream, time_refine=time_refine, pts_per_item=ppi)
+            api.pip_join(layer, pts, out_id, form=form, stream=stream, time_refine=time_refine, pts_per_item=ppi,
+                         **kn)
 
     for _ in range(warmup):
         one(False)
@@ -535,9 +553,12 @@ def join_leg(api, args, w, dev, stream, world, steps, warmup, peaks, baselines=T
     layer, layer_ms = build_layer(api, w, dev, stream)
     pts = torch.as_tensor(w.points, device=dev)
     n = pts.shape[0]
-    ppi = default_ppi(args)
+    t = tuned(args)
+    ppi = t["ppi"]
+    kn = dict(block=t["block"], edges_per_chunk=t["edges"])
     with ClockSampler(gpu_index(dist_env()[2])) as clk:
-        ms, st, outs = time_joins(api, layer, w, pts, args.form, steps, warmup, world, stream, ppi=ppi, clk=clk)
+        ms, st, outs = time_joins(api, layer, w, pts, args.form, steps, warmup, world, stream, ppi=ppi, clk=clk,
+                                  knobs=kn)
     clocks = clk.summary()
     ms_max = max_over_ranks(ms, world, dev)
     census = None
@@ -557,7 +578,7 @@ def join_leg(api, args, w, dev, stream, world, steps, warmup, peaks, baselines=T
     if baselines and args.form != "fp64":
         k64 = max(3, min(steps, 20))
         with ClockSampler(gpu_index(dist_env()[2])) as clk64:
-            ms64, st64, _ = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, stream, ppi=ppi, clk=clk64)
+            ms64, st64, _ = time_joins(api, layer, w, pts, "fp64", k64, 2, 1, stream, ppi=ppi, clk=clk64, knobs=kn)
         res["fp64_plain"] = {"value": n * k64 / (ms64 / 1000.0), "unit": "points/s", "ms_per_step": ms64 / k64,
                              "steps": k64, "roofline": roofline_of(w, "fp64", st64, ms64 / k64, peaks, census),
                              "clocks": clk64.summary()}
@@ -570,9 +591,10 @@ def join_leg(api, args, w, dev, stream, world, steps, warmup, peaks, baselines=T
         ke = max(3, min(steps, 20))
         if w.kind == "p2p":
             join_host = lambda: api.p2p_join_host(layer, hp, hid, hd, form=args.form, stream=stream,
-                                                  pts_per_item=ppi)
+                                                  pts_per_item=ppi, **kn)
         else:
-            join_host = lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream, pts_per_item=ppi)
+            join_host = lambda: api.pip_join_host(layer, hp, hid, form=args.form, stream=stream, pts_per_item=ppi,
+                                                  **kn)
         for _ in range(2):
             join_host()
         torch.cuda.synchronize()

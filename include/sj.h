@@ -84,14 +84,27 @@ enum {
     SJ_PERSISTENT = 1   /* same kernels (accepted for callers that ask for it)    */
 };
 
-/* Join options; a zeroed struct (or NULL) selects the defaults. */
+/* Join options; a zeroed struct (or NULL) selects the defaults.  The launch
+ * knobs (block, pts_per_item, edges_per_chunk) change speed only, never a
+ * result; paper_1403_0802_gb300/autotune.py times their combinations. */
 typedef struct {
     int32_t form;            /* SJ_FP64 (default) or SJ_FP32X                       */
     int32_t launch;          /* SJ_PER_REQUEST (default) or SJ_PERSISTENT           */
-    int32_t block;           /* reserved, 0 (refinement blocks are 4 warps; the grid
-                                is SMs x resident blocks, from the occupancy)      */
+    int32_t block;           /* warps per refinement block: 2, 4 or 8; 0 = 4.  The
+                                grid keeps the same number of resident warps (SMs x
+                                the occupancy of 4-warp blocks, in warps)          */
     int32_t pts_per_item;    /* points per work item, 1..128, 0 = default (128)    */
-    int32_t edges_per_chunk; /* reserved, 0                                         */
+    int32_t edges_per_chunk; /* edge budget of a work item: a cell whose points
+                                each test w > edges_per_chunk edges (PIP: the near
+                                edges of its boundary candidates; P2P: its segment
+                                list) is cut into items of
+                                max(min(pts_per_item, 8),
+                                    pts_per_item * edges_per_chunk / w) points, so
+                                that heavy cells yield more, smaller items (the work
+                                queue split by candidate-edge count).  0 = the
+                                default: 64 for polygon layers, no split for
+                                polyline layers; a value above every cell's work
+                                (e.g. INT32_MAX) turns the split off              */
     int32_t flags;           /* SJ_FLAG_* bits                                      */
 } sj_opts;
 

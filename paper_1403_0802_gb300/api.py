@@ -32,11 +32,12 @@ def _stream(stream) -> int | None:
     return stream.cuda_stream if isinstance(stream, torch.cuda.Stream) else int(stream)
 
 
-def _opts(form="fp64", launch="per_request", pts_per_item=0, time_refine=False, subcell=None) -> L.sj_opts:
+def _opts(form="fp64", launch="per_request", pts_per_item=0, time_refine=False, subcell=None, block=0,
+          edges_per_chunk=0) -> L.sj_opts:
     flags = L.SJ_FLAG_TIME_REFINE if time_refine else 0
     if subcell is not None:
         flags |= L.SJ_FLAG_SUBCELL_ON if subcell else L.SJ_FLAG_SUBCELL_OFF
-    return L.sj_opts(FORMS[form], LAUNCHES[launch], 0, int(pts_per_item), 0, flags)
+    return L.sj_opts(FORMS[form], LAUNCHES[launch], int(block), int(pts_per_item), int(edges_per_chunk), flags)
 
 
 def _dev(a, dtype, device="cuda") -> torch.Tensor:
@@ -136,13 +137,16 @@ def _points(pts) -> torch.Tensor:
 
 
 def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp64", launch: str = "per_request",
-             pts_per_item: int = 0, stream=None, time_refine: bool = False, subcell: bool | None = None) -> torch.Tensor:
+             pts_per_item: int = 0, stream=None, time_refine: bool = False, subcell: bool | None = None,
+             block: int = 0, edges_per_chunk: int = 0) -> torch.Tensor:
     """Polygon id (or -1) per point, int32 on the points' device (Sec. III.C).
-    subcell: order points by sub-cell inside their cells (None: the library's
-    choice); results do not depend on it."""
+    Launch knobs (results do not depend on them): subcell orders points by
+    sub-cell inside their cells (None: the library's choice), block = warps per
+    refinement block (0: 4), edges_per_chunk = the edge budget of a work item
+    (0: the library default, 64 for polygon layers)."""
     p = _points(pts)
     out = torch.empty(p.shape[0], dtype=torch.int32, device=p.device) if out is None else out
-    o = _opts(form, launch, pts_per_item, time_refine, subcell)
+    o = _opts(form, launch, pts_per_item, time_refine, subcell, block, edges_per_chunk)
     L.check(L.lib().sj_pip_join(layer.handle, _ptr(p), p.shape[0], _ptr(out), C.byref(o), _stream(stream)),
             "sj_pip_join")
     return out
@@ -150,14 +154,15 @@ def pip_join(layer: Layer, pts, out: torch.Tensor | None = None, form: str = "fp
 
 def p2p_join(layer: Layer, pts, out_id: torch.Tensor | None = None, out_d: torch.Tensor | None = None,
              form: str = "fp64", launch: str = "per_request", pts_per_item: int = 0, stream=None,
-             time_refine: bool = False, window: float | None = None, subcell: bool | None = None):
+             time_refine: bool = False, window: float | None = None, subcell: bool | None = None,
+             block: int = 0, edges_per_chunk: int = 0):
     """(nearest polyline id or -1, distance or +inf) per point (Sec. III.B); window (<= the layer's D)
-    replaces D for this call (sj_p2p_join_window); subcell as in pip_join."""
+    replaces D for this call (sj_p2p_join_window); launch knobs as in pip_join."""
     p = _points(pts)
     n = p.shape[0]
     out_id = torch.empty(n, dtype=torch.int32, device=p.device) if out_id is None else out_id
     out_d = torch.empty(n, dtype=torch.float64, device=p.device) if out_d is None else out_d
-    o = _opts(form, launch, pts_per_item, time_refine, subcell)
+    o = _opts(form, launch, pts_per_item, time_refine, subcell, block, edges_per_chunk)
     if window is None:
         L.check(L.lib().sj_p2p_join(layer.handle, _ptr(p), n, _ptr(out_id), _ptr(out_d), C.byref(o),
                                     _stream(stream)), "sj_p2p_join")
@@ -192,12 +197,12 @@ def pip_census(layer: Layer, pts, stream=None) -> tuple[int, int]:
 
 
 def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, form: str = "fp64",
-                  stream=None, pts_per_item: int = 0) -> np.ndarray:
+                  stream=None, pts_per_item: int = 0, block: int = 0, edges_per_chunk: int = 0) -> np.ndarray:
     """Same as pip_join from host memory (copies in and out; synchronous)."""
     p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
     n = p.shape[0]
     out = np.empty(n, np.int32) if out is None else out
-    o = _opts(form, pts_per_item=pts_per_item)
+    o = _opts(form, pts_per_item=pts_per_item, block=block, edges_per_chunk=edges_per_chunk)
     pp = p.data_ptr() if isinstance(p, torch.Tensor) else p.ctypes.data
     op = out.data_ptr() if isinstance(out, torch.Tensor) else out.ctypes.data
     L.check(L.lib().sj_pip_join_host(layer.handle, pp, n, op, C.byref(o), _stream(stream)), "sj_pip_join_host")
@@ -205,13 +210,13 @@ def pip_join_host(layer: Layer, pts: np.ndarray, out: np.ndarray | None = None, 
 
 
 def p2p_join_host(layer: Layer, pts, out_id=None, out_d=None, form: str = "fp64", stream=None,
-                  pts_per_item: int = 0, window: float | None = None):
+                  pts_per_item: int = 0, window: float | None = None, block: int = 0, edges_per_chunk: int = 0):
     """Same as p2p_join from host memory (copies in and out; synchronous); window as in p2p_join."""
     p = np.ascontiguousarray(pts, dtype=np.float64) if not isinstance(pts, torch.Tensor) else pts
     n = p.shape[0]
     out_id = np.empty(n, np.int32) if out_id is None else out_id
     out_d = np.empty(n, np.float64) if out_d is None else out_d
-    o = _opts(form, pts_per_item=pts_per_item)
+    o = _opts(form, pts_per_item=pts_per_item, block=block, edges_per_chunk=edges_per_chunk)
     ptr = lambda a: a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
     if window is None:
         L.check(L.lib().sj_p2p_join_host(layer.handle, ptr(p), n, ptr(out_id), ptr(out_d), C.byref(o),

@@ -1,13 +1,20 @@
 """Autotuner for the join's launch knobs.
 
-Knobs: points per work item (how many points of a cell one warp refines
-against the cell's staged candidates), the filter grid resolution (Sec. III.A:
-a finer grid gives fewer false candidates but more cells and smaller items --
-the paper's own trade-off, left to tuning), and the arithmetic form.  Each
-setting is timed with CUDA events over a few joins of the given points after a
-warm-up; the fastest setting is returned with the whole table.
+Knobs (none changes a result):
+  * points per work item -- how many points of a cell one warp refines
+    against the cell's staged candidates;
+  * edges per chunk -- the edge budget of a work item: a cell whose points
+    each test more edges is cut into smaller items, so heavy cells (complex
+    polygons, Sec. IV.C; dense polyline cells) spread over more warps;
+  * block -- warps per refinement block (2, 4 or 8);
+  * the filter grid resolution (Sec. III.A: a finer grid gives fewer false
+    candidates but more cells and smaller items -- the paper's own
+    trade-off, left to tuning);
+  * the arithmetic form.
+Each setting is timed with CUDA events over a few joins of the given points
+after a warm-up; the fastest setting is returned with the whole table.
 
-    python -m paper_1403_0802_gb300.autotune --workload p2p --points 2000000
+    python -m paper_1403_0802_gb300.autotune --workload pip3 --layer 2 --points 10000000
 """
 from __future__ import annotations
 
@@ -21,18 +28,20 @@ import torch
 from . import api, synth
 
 
-def time_join(layer, pts, kind: str, form: str, ppi: int, steps: int = 8, warmup: int = 2) -> float:
+def time_join(layer, pts, kind: str, form: str, ppi: int, steps: int = 8, warmup: int = 2, block: int = 0,
+              edges_per_chunk: int = 0) -> float:
     """Mean milliseconds per join."""
     n = pts.shape[0]
     out_id = torch.empty(n, dtype=torch.int32, device=pts.device)
     out_d = torch.empty(n, dtype=torch.float64, device=pts.device)
     stream = torch.cuda.current_stream()
+    kw = dict(form=form, pts_per_item=ppi, stream=stream, block=block, edges_per_chunk=edges_per_chunk)
 
     def one():
         if kind == "p2p":
-            api.p2p_join(layer, pts, out_id, out_d, form=form, pts_per_item=ppi, stream=stream)
+            api.p2p_join(layer, pts, out_id, out_d, **kw)
         else:
-            api.pip_join(layer, pts, out_id, form=form, pts_per_item=ppi, stream=stream)
+            api.pip_join(layer, pts, out_id, **kw)
 
     for _ in range(warmup):
         one()
@@ -46,7 +55,7 @@ def time_join(layer, pts, kind: str, form: str, ppi: int, steps: int = 8, warmup
 
 
 def autotune(w: synth.Workload, grids=(512, 1024, 2048), ppis=(16, 32, 64, 128), forms=("fp32x",),
-             steps: int = 8) -> dict:
+             blocks=(4,), edges=(0,), steps: int = 8) -> dict:
     pts = torch.as_tensor(w.points, device="cuda")
     table = []
     for g in grids:
@@ -61,10 +70,10 @@ def autotune(w: synth.Workload, grids=(512, 1024, 2048), ppis=(16, 32, 64, 128),
             layer = api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, grid)
         build_ms = (time.perf_counter() - t0) * 1e3
         with layer:
-            for form, ppi in itertools.product(forms, ppis):
-                ms = time_join(layer, pts, w.kind, form, ppi, steps=steps)
-                table.append({"grid": g, "pts_per_item": ppi, "form": form, "ms": ms,
-                              "points_per_s": len(w.points) / (ms / 1e3), "layer_build_ms": build_ms})
+            for form, ppi, nw, epc in itertools.product(forms, ppis, blocks, edges):
+                ms = time_join(layer, pts, w.kind, form, ppi, steps=steps, block=nw, edges_per_chunk=epc)
+                table.append({"grid": g, "pts_per_item": ppi, "block": nw, "edges_per_chunk": epc, "form": form,
+                              "ms": ms, "points_per_s": len(w.points) / (ms / 1e3), "layer_build_ms": build_ms})
     best = min(table, key=lambda r: r["ms"])
     return {"workload": w.name, "best": best, "table": table}
 
@@ -76,6 +85,8 @@ def main():
     ap.add_argument("--layer", type=int, default=1)
     ap.add_argument("--grids", default="512,1024,2048")
     ap.add_argument("--ppis", default="16,32,64,128")
+    ap.add_argument("--blocks", default="2,4,8")
+    ap.add_argument("--edges", default="0,64,256,1024")
     ap.add_argument("--forms", default="fp32x")
     a = ap.parse_args()
     if a.workload == "p2p":
@@ -86,8 +97,9 @@ def main():
         w = synth.pip_tiles(n_points=a.points, layer=a.layer)
     else:
         w = synth.p2p_walks_lognormal(n_points=a.points)
-    res = autotune(w, grids=[int(x) for x in a.grids.split(",")], ppis=[int(x) for x in a.ppis.split(",")],
-                   forms=a.forms.split(","))
+    ints = lambda x: [int(v) for v in x.split(",")]
+    res = autotune(w, grids=ints(a.grids), ppis=ints(a.ppis), forms=a.forms.split(","), blocks=ints(a.blocks),
+                   edges=ints(a.edges))
     print(json.dumps(res))
 
 

@@ -206,7 +206,8 @@ static void layer_free(sj_layer *L) {
     void *ptrs[] = {L->verts, L->vsplit, L->obj_voff, L->nxt, L->prv, L->ring_off, L->poly_ring_off, L->seg_e64,
                     L->seg_inv64, L->seg32, L->mbb, L->cand_start, L->cand_ids, L->stats, L->cell_keys,
                     L->frames, L->cseg_start, L->cseg_ids, L->cell_algo, L->cseg_rec, L->prow_base, L->prow_r0,
-                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls, L->cell_res, L->bnear_start, L->bnear_ids,
+                    L->prow_start, L->pedge_ids, L->pedge_rec, L->cand_cls, L->cell_res, L->cell_work,
+                    L->bnear_start, L->bnear_ids,
                     L->bnear_rec, L->bnear_key, L->bnear_h, L->bflip_start, L->bflip_len, L->bflip_keys};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -317,8 +318,10 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
         L->MS = 0;
         CUDA_TRY(dalloc(&L->cseg_ids, 0));
         CUDA_TRY(dalloc(&L->cseg_rec, 0));
+        CUDA_TRY(dalloc(&L->cell_work, (size_t)G));
         CUDA_TRY(cudaMemsetAsync(L->cseg_start, 0, sizeof(int) * ((size_t)G + 1), s));
         CUDA_TRY(cudaMemsetAsync(L->cell_algo, 0, sizeof(int) * (size_t)G, s));
+        CUDA_TRY(cudaMemsetAsync(L->cell_work, 0, sizeof(int) * (size_t)G, s));
         CUDA_TRY(cudaStreamSynchronize(s));
         return SJ_OK;
     }
@@ -365,6 +368,8 @@ static sj_status build_seg_lists(sj_layer *L, cudaStream_t s) {
     CUDA_TRY(dalloc(&L->cseg_rec, 2 * (size_t)MS));
     CUDA_TRY(launch_cseg_records(L->cseg_start, L->cseg_ids, L->g, L->frames, L->frames + L->g.nx, L->vsplit,
                                  L->seg32, L->cseg_rec, s));
+    CUDA_TRY(dalloc(&L->cell_work, (size_t)G));
+    CUDA_TRY(launch_cell_work_p2p(L->cseg_start, G, L->cell_work, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
 }
@@ -382,6 +387,8 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
         CUDA_TRY(dalloc(&L->bnear_ids, 0));
         CUDA_TRY(dalloc(&L->bnear_rec, 0));
         CUDA_TRY(dalloc(&L->bnear_key, 0));
+        CUDA_TRY(dalloc(&L->cell_work, (size_t)L->g.G));
+        CUDA_TRY(cudaMemsetAsync(L->cell_work, 0, sizeof(int) * (size_t)L->g.G, s));
         CUDA_TRY(dalloc(&L->bflip_keys, 0));
         CUDA_TRY(cudaMemsetAsync(L->bnear_start, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(L->bflip_start, 0, sizeof(int), s));
@@ -447,6 +454,8 @@ static sj_status build_boundary_lists(sj_layer *L, double delta, cudaStream_t s)
     // near lists ordered by lower y, with their keys and y-extents (the
     // refinement's window search on long lists), then the staging records
     CUDA_TRY(launch_pip_near_sort(L->bnear_start, M, L->bnear_ids, L->nxt, L->vsplit, L->bnear_key, L->bnear_h, s));
+    CUDA_TRY(dalloc(&L->cell_work, (size_t)L->g.G));
+    CUDA_TRY(launch_cell_work_pip(L->cand_start, L->cand_cls, L->bnear_start, L->g.G, L->cell_work, s));
     if (L->MN > 0) CUDA_TRY(launch_prow_records(L->bnear_ids, (long long)L->MN, L->nxt, L->vsplit, L->bnear_rec, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return SJ_OK;
@@ -749,9 +758,11 @@ enum { RES_PERM = 0, RES_IDS, RES_F, RES_D };
 
 // with_spts: also a cell-ordered copy of the points (else the refinement reads
 // the input points through perm).
+// ch_min: the smallest work item (cell_chunk's floor when items are split by
+// edge budget, else ch).
 static void carve(Scratch &s, JoinBufs &b, int64_t N, int G, int ch, bool need_fb, bool with_spts = true,
-                  int res = RES_PERM, int lS = 0) {
-    size_t max_items = (size_t)(N / ch) + (size_t)std::min<int64_t>(G, N) + 1;
+                  int res = RES_PERM, int lS = 0, int ch_min = 0) {
+    size_t max_items = (size_t)(N / (ch_min > 0 ? ch_min : ch)) + (size_t)std::min<int64_t>(G, N) + 1;
     b.cnt = s.take<int>(((size_t)G << lS) + 1);
     b.sub_start = lS ? s.take<int>((size_t)G << lS) : nullptr;
     b.cell_start = s.take<int>((size_t)G + 1);
@@ -789,6 +800,15 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
         return fail(SJ_ERR_INVALID, "SJ_FP32X needs grid coordinates below 1e30 in magnitude; use SJ_FP64");
     int ch = (o && o->pts_per_item) ? o->pts_per_item : 128;
     if (ch < 1 || ch > MAX_CH) return fail(SJ_ERR_INVALID, "pts_per_item must be in 1..128");
+    const int nw = (o && o->block) ? o->block : 4;
+    if (nw != 2 && nw != 4 && nw != 8) return fail(SJ_ERR_INVALID, "block must be 0, 2, 4 or 8 (warps per block)");
+    int budget = o ? o->edges_per_chunk : 0;
+    if (budget < 0) return fail(SJ_ERR_INVALID, "edges_per_chunk must be >= 0");
+    // default: polygon layers split heavy cells at 64 edges per point (the
+    // autotuner's best on both tilings at 100 M points: heavy-tail layer
+    // 8.1 -> 6.5 ms, 40,000 tiles 5.2 -> 4.8 ms); polyline layers do not (no
+    // setting was faster on the walks)
+    if (budget == 0 && kind == KIND_PIP) budget = 64;
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev != L->device) return fail(SJ_ERR_INVALID, "layer belongs to another device");
@@ -824,10 +844,12 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
 
     JoinBufs b;
     const int res = kind == KIND_PIP ? RES_IDS : (form == SJ_FP32X ? RES_F : RES_D);
-    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res, lS); });
+    const bool split = budget > 0 && L->cell_work;   // items sized by the cells' edge work
+    const int ch_min = split ? std::min(ch, 8) : ch;
+    size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res, lS, ch_min); });
     Scratch sc;
     CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
-    carve(sc, b, N, G, ch, need_fb, false, res, lS);
+    carve(sc, b, N, G, ch, need_fb, false, res, lS, ch_min);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * (((size_t)G << lS) + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
 
@@ -842,6 +864,8 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ba.spts = b.spts;
     ba.cand_start = L->cand_start;
     ba.ch = ch;
+    ba.cell_work = split ? L->cell_work : nullptr;
+    ba.budget = split ? budget : 0;
     ba.items = b.items;
     ba.block_sums = b.block_sums;
     ba.bs_cap = bucket_scan_blocks(G);
@@ -885,6 +909,8 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ra.spts = b.spts;
     ra.pts = (const double2 *)pts;
     ra.ch = ch;
+    ra.cell_work = ba.cell_work;
+    ra.budget = ba.budget;
     ra.res_id = b.res_id;   // cell-ordered results, every slot of a refined cell written
     ra.resf = b.resf;
     ra.resd = b.resd;
@@ -900,8 +926,8 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
         if (e == cudaSuccess) e = cudaEventRecord(ev0, s);
     }
     if (e == cudaSuccess) {
-        if (kind == KIND_PIP) e = launch_pip_refine(ra, form, 4, di->sms * di->pip_bps[form], s);
-        else e = launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s);
+        if (kind == KIND_PIP) e = launch_pip_refine(ra, form, nw, di->sms * di->pip_bps[form], s);
+        else e = launch_p2p_refine(ra, form, nw, di->sms * di->p2p_bps[form], s);
     }
     if (timed && ev1) {   // the refinement launch alone
         if (e == cudaSuccess) e = cudaEventRecord(ev1, s);

@@ -255,6 +255,8 @@ struct BucketLoad {
     const int *cand_start;
     int ch;
     int lS;           // log2 of the sub-cells per cell (0: none)
+    const int *cell_work;
+    int budget;
     __device__ int2 operator()(int c) const {
         int np = 0;
         if (lS == 0) {
@@ -264,7 +266,10 @@ struct BucketLoad {
             for (int k = 0; k < (1 << lS); ++k) np += q[k];
         }
         int ni = 0;
-        if (cand_start && np > 0 && cand_start[c + 1] > cand_start[c]) ni = (np + ch - 1) / ch;
+        if (cand_start && np > 0 && cand_start[c + 1] > cand_start[c]) {
+            const int cc = cell_chunk(ch, budget > 0 ? cell_work[c] : 0, budget);
+            ni = (np + cc - 1) / cc;
+        }
         return make_int2(np, ni);
     }
 };
@@ -276,12 +281,16 @@ struct BucketApply {
     const int *cnt;   // with sub-cells: their counters and first slots
     int *sub_start;
     int lS;
+    const int *cell_work;
+    int budget;
     __device__ void operator()(int c, int2 ex, int2 v, int n) const {
         cell_start[c] = ex.x;
         if (cell_base) cell_base[c] = v.y > 0 ? ex.x : -1;
         if (c == n - 1) cell_start[n] = ex.x + v.x;
-        if (items)
-            for (int t = 0; t < v.y; ++t) items[ex.y + t] = make_int2(c, t * ch);
+        if (items && v.y > 0) {
+            const int cc = cell_chunk(ch, budget > 0 ? cell_work[c] : 0, budget);
+            for (int t = 0; t < v.y; ++t) items[ex.y + t] = make_int2(c, t * cc);
+        }
         if (lS > 0) {
             const size_t b = (size_t)c << lS;
             const bool none = cell_base && v.y == 0;
@@ -378,9 +387,9 @@ static int stream_blocks(long long n, int per_block, int cap) {
 // and totals.  Grid size depends only on G, so the launch can be replayed.
 cudaError_t launch_bucket_scan(const BucketArgs &a, cudaStream_t s) {
     const int lS = a.sub_lx + a.sub_ly;
-    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch, lS},
-                    BucketApply{a.cell_start, a.items, a.ch, a.cell_base, a.cnt, a.sub_start, lS}, a.g.G,
-                    a.block_sums, a.bs_cap, a.totals, s);
+    return run_scan(BucketLoad{a.cnt, a.cand_start, a.ch, lS, a.cell_work, a.budget},
+                    BucketApply{a.cell_start, a.items, a.ch, a.cell_base, a.cnt, a.sub_start, lS, a.cell_work, a.budget},
+                    a.g.G, a.block_sums, a.bs_cap, a.totals, s);
 }
 
 // Packed records: one gather per point.  FP32X distances widen exactly.
@@ -428,7 +437,8 @@ cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d
 
 cudaError_t launch_bucket(const BucketArgs &a, cudaStream_t s) {
     int nb = stream_blocks(a.n, 256, 152 * 32);
-    if (a.sub_lx < 0 || a.sub_ly < 0 || a.sub_lx > 3 || a.sub_ly > 3 || ((a.sub_lx + a.sub_ly) && !a.sub_start))
+    if (a.sub_lx < 0 || a.sub_ly < 0 || a.sub_lx > 3 || a.sub_ly > 3 || ((a.sub_lx + a.sub_ly) && !a.sub_start) ||
+        (a.budget > 0 && !a.cell_work))
         return cudaErrorInvalidValue;
     k_cell_hist<<<nb, 256, 0, s>>>(a);
     cudaError_t e = launch_bucket_scan(a, s);
@@ -713,6 +723,17 @@ __global__ void k_cseg_records(const int *cseg_start, const int *cseg_ids, int G
             rec[2 * (size_t)g + 1] = make_float4(e.z, e.w, mag, __int_as_float(i));
         }
     }
+}
+
+// Per-point segment work of each cell of a polyline layer: its list length.
+__global__ void k_cell_work_p2p(const int *cseg_start, int G, int *work) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x)
+        work[c] = cseg_start[c + 1] - cseg_start[c];
+}
+
+cudaError_t launch_cell_work_p2p(const int *cseg_start, int G, int *work, cudaStream_t s) {
+    k_cell_work_p2p<<<stream_blocks(G, 256, 8192), 256, 0, s>>>(cseg_start, G, work);
+    return cudaGetLastError();
 }
 
 // Per cell: the number of segments of its candidate polylines (the tests the

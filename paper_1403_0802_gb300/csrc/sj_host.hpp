@@ -57,6 +57,7 @@ struct sj_layer {
     float4 *pedge_rec = nullptr; // [2 ME] FP32X staging records: vsplit of the edge's two ends
     unsigned char *cand_cls = nullptr;   // [M] per candidate entry: 0 boundary, 1 inside, 2 outside
     int *cell_res = nullptr;             // [G] result of every point of a fully classified cell, or CELL_REFINE
+    int *cell_work = nullptr;            // [G] per-point edge / segment work of each cell (item sizes)
     // PIP boundary entries (class 0): near edges (x-range meets the cell's column
     // widened by delta) and the flip keys of the far-right edges' parity in y
     int64_t MN = 0, MF = 0;

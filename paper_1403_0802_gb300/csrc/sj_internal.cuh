@@ -152,6 +152,18 @@ __device__ __forceinline__ void copy_async_wait_all() {
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
+// Points per work item of cell c: the join's chunk size ch, reduced for cells
+// whose points each test many edges / segments (work = the cell's list
+// length) so that points x work stays within ch x budget -- the work queue is
+// split by candidate-edge count, heavy cells yielding more, smaller items --
+// but never below min(ch, 8) points (budget 0: ch for every cell).
+__host__ __device__ __forceinline__ int cell_chunk(int ch, int work, int budget) {
+    if (budget <= 0 || work <= budget) return ch;
+    const long long c = (long long)ch * budget / work;
+    const int lo = ch < 8 ? ch : 8;
+    return c < lo ? lo : (c > ch ? ch : (int)c);
+}
+
 // Lanes per point group for a chunk of `nw` work units (edges / segments) and
 // `np` points: the power of two SG in {1..32} that minimises the number of
 // warp iterations ceil(np / (32 / SG)) * (ceil(nw / SG) + reduction steps).
@@ -259,7 +271,9 @@ struct RefineArgs {
     float eps_abs;           // absolute term of the split-coordinate rounding bound
     const float *frame_x;    // [nx] FP32 cell frame origins along x
     const float *frame_y;    // [ny]
-    int ch;                  // points per work item
+    int ch;                  // points per work item (at most; see cell_chunk)
+    const int *cell_work;    // [G] per-point edge / segment work of each cell (or null)
+    int budget;              // edge budget per point of an item (0: none)
     int *out_id;
     double *out_d;
     int *res_id;             // when set: results in sorted order for every slot
@@ -300,6 +314,9 @@ cudaError_t launch_pip_near_sort(const int *near_start, int M, int *ids, const i
                                  float *keys, float *h, cudaStream_t s);
 
 // PIP cell classification (layer build): one class per candidate entry.
+cudaError_t launch_cell_work_pip(const int *cand_start, const unsigned char *cls, const int *near_start, int G,
+                                 int *work, cudaStream_t s);
+cudaError_t launch_cell_work_p2p(const int *cseg_start, int G, int *work, cudaStream_t s);
 cudaError_t launch_cell_result(const int *cand_start, const int *cand_ids, const unsigned char *cls, int G, int *res,
                                cudaStream_t s);
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
@@ -324,6 +341,8 @@ struct BucketArgs {
     double2 *spts;       // [n] cell-ordered copy of the points, or null (not written)
     const int *cand_start;  // layer candidates (null: no work items)
     int ch;
+    const int *cell_work;   // with budget > 0: work items of cell_chunk(ch, cell_work[c], budget) points
+    int budget;
     int2 *items;         // work items or null
     int2 *block_sums;    // scan scratch
     size_t bs_cap;       // its capacity in int2 (launches fail when it is too small)

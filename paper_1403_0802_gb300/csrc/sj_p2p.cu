@@ -235,8 +235,8 @@ __device__ __forceinline__ void p2p_compute(P2PSmem<FP32> &s, int np, int ns, in
 // PW = false, whose code has no window load at all.  Eight blocks per SM is
 // the shared-memory limit already; saying so keeps the register allocator at
 // 64 registers without spills.
-template <bool FP32, bool PW>
-__global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) {
+template <bool FP32, bool PW, int NW>
+__global__ void __launch_bounds__(NW * 32, 32 / NW) k_p2p_refine(RefineArgs a) {
     using T = typename std::conditional<FP32, float, double>::type;
     constexpr int SMAX = P2PSmem<FP32>::SMAX;
     extern __shared__ __align__(16) unsigned char p2p_smem_raw[];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
     // items are mostly chunks of one cell, whose segment records are then
     // still in L1 for the second chunk.
     const int claim = a.claim > 1 ? a.claim : 1;
-    int it = blockIdx.x * P2P_WARPS + w, it_end = it + 1;
+    int it = blockIdx.x * NW + w, it_end = it + 1;
     if (a.work_next) {
         int t0 = 0;
         if (lane == 0) t0 = atomicAdd(a.work_next, claim);
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
         cs1 = a.cell_start[item.x + 1];
     }
     while (it < n_items) {
-        int it_next = it + gridDim.x * P2P_WARPS;
+        int it_next = it + gridDim.x * NW;
         const bool in_claim = it + 1 < it_end;
         if (a.work_next) {
             if (in_claim) it_next = it + 1;
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(P2P_WARPS * 32, 8) k_p2p_refine(RefineArgs a) 
         ++c_items;
         const int c = item.x;
         const int j0 = cs0 + item.y;
-        const int np = min(a.ch, cs1 - j0);
+        const int np = min(cell_chunk(a.ch, a.budget > 0 ? a.cell_work[c] : 0, a.budget), cs1 - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
@@ -526,36 +526,46 @@ __global__ void __launch_bounds__(256) k_p2p_recheck(RefineArgs a) {
     }
 }
 
-template <bool FP32>
+template <bool FP32, int NW>
 static size_t p2p_smem_bytes() {
-    return sizeof(P2PSmem<FP32>) * P2P_WARPS;
+    return sizeof(P2PSmem<FP32>) * NW;
 }
 
-template <bool FP32, bool PW>
+template <bool FP32, bool PW, int NW>
 static cudaError_t p2p_prepare() {
     static bool done = false;   // per process; the attribute is per function
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_p2p_refine<FP32, PW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)p2p_smem_bytes<FP32>());
+        cudaError_t e = cudaFuncSetAttribute(k_p2p_refine<FP32, PW, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)p2p_smem_bytes<FP32, NW>());
         if (e != cudaSuccess) return e;
         done = true;
     }
     return cudaSuccess;
 }
 
-template <bool FP32, bool PW>
+template <bool FP32, bool PW, int NW>
 static cudaError_t p2p_launch(const RefineArgs &a, int blocks, cudaStream_t s) {
-    cudaError_t e = p2p_prepare<FP32, PW>();
+    cudaError_t e = p2p_prepare<FP32, PW, NW>();
     if (e != cudaSuccess) return e;
-    k_p2p_refine<FP32, PW><<<blocks, P2P_WARPS * 32, p2p_smem_bytes<FP32>(), s>>>(a);
+    k_p2p_refine<FP32, PW, NW><<<blocks, NW * 32, p2p_smem_bytes<FP32, NW>(), s>>>(a);
     return cudaGetLastError();
 }
 
+template <bool FP32, bool PW>
+static cudaError_t p2p_launch_nw(const RefineArgs &a, int nw, int blocks, cudaStream_t s) {
+    if (nw == 2) return p2p_launch<FP32, PW, 2>(a, blocks, s);
+    if (nw == 8) return p2p_launch<FP32, PW, 8>(a, blocks, s);
+    return p2p_launch<FP32, PW, P2P_WARPS>(a, blocks, s);
+}
+
+// blocks: the grid for blocks of P2P_WARPS warps (resident blocks x SMs); a
+// block of warps_per_block (2, 4 or 8) warps gets the same number of warps.
 cudaError_t launch_p2p_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
-    (void)warps_per_block;
+    const int nw = (warps_per_block == 2 || warps_per_block == 8) ? warps_per_block : P2P_WARPS;
+    blocks = (int)(((long long)blocks * P2P_WARPS + nw - 1) / nw);
     const bool pw = a.win && a.win_on;
-    if (form == SJ_FP32X) return pw ? p2p_launch<true, true>(a, blocks, s) : p2p_launch<true, false>(a, blocks, s);
-    return pw ? p2p_launch<false, true>(a, blocks, s) : p2p_launch<false, false>(a, blocks, s);
+    if (form == SJ_FP32X) return pw ? p2p_launch_nw<true, true>(a, nw, blocks, s) : p2p_launch_nw<true, false>(a, nw, blocks, s);
+    return pw ? p2p_launch_nw<false, true>(a, nw, blocks, s) : p2p_launch_nw<false, false>(a, nw, blocks, s);
 }
 
 cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s) {
@@ -566,13 +576,13 @@ cudaError_t launch_p2p_recheck(const RefineArgs &a, int blocks, cudaStream_t s) 
 int p2p_blocks_per_sm(int form) {
     int n = 0;
     if (form == SJ_FP32X) {
-        if (p2p_prepare<true, false>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true, false>, P2P_WARPS * 32,
-                                                      p2p_smem_bytes<true>());
+        if (p2p_prepare<true, false, P2P_WARPS>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<true, false, P2P_WARPS>, P2P_WARPS * 32,
+                                                      p2p_smem_bytes<true, P2P_WARPS>());
     } else {
-        if (p2p_prepare<false, false>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false, false>, P2P_WARPS * 32,
-                                                      p2p_smem_bytes<false>());
+        if (p2p_prepare<false, false, P2P_WARPS>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_p2p_refine<false, false, P2P_WARPS>, P2P_WARPS * 32,
+                                                      p2p_smem_bytes<false, P2P_WARPS>());
     }
     return n > 0 ? n : 1;
 }

@@ -233,8 +233,8 @@ __device__ __forceinline__ unsigned long long pip_compute(PipSmem<FP32> &s, cons
     return tests;
 }
 
-template <bool FP32>
-__global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) {
+template <bool FP32, int NW>
+__global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
     constexpr int SMAX = PipSmem<FP32>::SMAX;
     extern __shared__ __align__(16) unsigned char pip_smem_raw[];
     const int lane = lane_id(), w = threadIdx.x >> 5;
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
     // a.claim consecutive items per counter update (mostly chunks of one
     // cell, whose staged records are then still in L1).
     const int claim = a.claim > 1 ? a.claim : 1;
-    int it = blockIdx.x * PIP_WARPS + w, it_end = it + 1;
+    int it = blockIdx.x * NW + w, it_end = it + 1;
     if (a.work_next) {
         int t0 = 0;
         if (lane == 0) t0 = atomicAdd(a.work_next, claim);
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
         it_end = it + claim;
     }
     while (it < n_items) {
-        int it_next = it + gridDim.x * PIP_WARPS;
+        int it_next = it + gridDim.x * NW;
         const bool in_claim = it + 1 < it_end;
         if (a.work_next) {
             if (in_claim) it_next = it + 1;
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(PIP_WARPS * 32, 7) k_pip_refine(RefineArgs a) 
         const int2 item = a.items[it];
         const int c = item.x;
         const int j0 = a.cell_start[c] + item.y;
-        const int np = min(a.ch, a.cell_start[c + 1] - j0);
+        const int np = min(cell_chunk(a.ch, a.budget > 0 ? a.cell_work[c] : 0, a.budget), a.cell_start[c + 1] - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
@@ -549,6 +549,26 @@ cudaError_t launch_cell_result(const int *cand_start, const int *cand_ids, const
     return cudaGetLastError();
 }
 
+// Per-point edge work of each cell of a polygon layer (the split of work
+// items by candidate-edge count): the near edges of its boundary candidates,
+// a long list (searched per point) counted as LONG_NEAR.
+__global__ void k_cell_work_pip(const int *cand_start, const unsigned char *cls, const int *near_start, int G,
+                                int *work) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < G; c += gridDim.x * blockDim.x) {
+        long long w = 0;
+        for (int k = cand_start[c]; k < cand_start[c + 1]; ++k)
+            if (cls[k] == 0) w += min(near_start[k + 1] - near_start[k], LONG_NEAR);
+        work[c] = (int)min(w, 2147483647LL);
+    }
+}
+
+cudaError_t launch_cell_work_pip(const int *cand_start, const unsigned char *cls, const int *near_start, int G,
+                                 int *work, cudaStream_t s) {
+    const int nb = (int)std::max<long long>(1, std::min<long long>(((long long)G + 255) / 256, 152LL * 32));
+    k_cell_work_pip<<<nb, 256, 0, s>>>(cand_start, cls, near_start, G, work);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
                                 const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
                                 const double2 *verts, double delta, unsigned char *cls, cudaStream_t s) {
@@ -782,45 +802,56 @@ cudaError_t launch_pip_census(const RefineArgs &a, const double2 *pts, int n, un
     return cudaGetLastError();
 }
 
-template <bool FP32>
+template <bool FP32, int NW>
 static size_t pip_smem_bytes() {
-    return sizeof(PipSmem<FP32>) * PIP_WARPS;
+    return sizeof(PipSmem<FP32>) * NW;
 }
 
-template <bool FP32>
+template <bool FP32, int NW>
 static cudaError_t pip_prepare() {
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(k_pip_refine<FP32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)pip_smem_bytes<FP32>());
+        cudaError_t e = cudaFuncSetAttribute(k_pip_refine<FP32, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)pip_smem_bytes<FP32, NW>());
         if (e != cudaSuccess) return e;
         done = true;
     }
     return cudaSuccess;
 }
 
-cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
-    (void)warps_per_block;
-    cudaError_t e;
-    if (form == SJ_FP32X) {
-        if ((e = pip_prepare<true>()) != cudaSuccess) return e;
-        k_pip_refine<true><<<blocks, PIP_WARPS * 32, pip_smem_bytes<true>(), s>>>(a);
-    } else {
-        if ((e = pip_prepare<false>()) != cudaSuccess) return e;
-        k_pip_refine<false><<<blocks, PIP_WARPS * 32, pip_smem_bytes<false>(), s>>>(a);
-    }
+template <bool FP32, int NW>
+static cudaError_t pip_launch(const RefineArgs &a, int blocks, cudaStream_t s) {
+    cudaError_t e = pip_prepare<FP32, NW>();
+    if (e != cudaSuccess) return e;
+    k_pip_refine<FP32, NW><<<blocks, NW * 32, pip_smem_bytes<FP32, NW>(), s>>>(a);
     return cudaGetLastError();
+}
+
+// blocks: the grid for blocks of PIP_WARPS warps; a block of warps_per_block
+// (2, 4 or 8) warps gets the same number of warps.
+cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s) {
+    const int nw = (warps_per_block == 2 || warps_per_block == 8) ? warps_per_block : PIP_WARPS;
+    blocks = (int)(((long long)blocks * PIP_WARPS + nw - 1) / nw);
+    if (form == SJ_FP32X) {
+        if (nw == 2) return pip_launch<true, 2>(a, blocks, s);
+        if (nw == 8) return pip_launch<true, 8>(a, blocks, s);
+        return pip_launch<true, PIP_WARPS>(a, blocks, s);
+    }
+    if (nw == 2) return pip_launch<false, 2>(a, blocks, s);
+    if (nw == 8) return pip_launch<false, 8>(a, blocks, s);
+    return pip_launch<false, PIP_WARPS>(a, blocks, s);
 }
 
 int pip_blocks_per_sm(int form) {
     int n = 0;
     if (form == SJ_FP32X) {
-        if (pip_prepare<true>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<true>, PIP_WARPS * 32, pip_smem_bytes<true>());
+        if (pip_prepare<true, PIP_WARPS>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<true, PIP_WARPS>, PIP_WARPS * 32,
+                                                      pip_smem_bytes<true, PIP_WARPS>());
     } else {
-        if (pip_prepare<false>() != cudaSuccess) return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<false>, PIP_WARPS * 32,
-                                                      pip_smem_bytes<false>());
+        if (pip_prepare<false, PIP_WARPS>() != cudaSuccess) return 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_pip_refine<false, PIP_WARPS>, PIP_WARPS * 32,
+                                                      pip_smem_bytes<false, PIP_WARPS>());
     }
     return n > 0 ? n : 1;
 }
