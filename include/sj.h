@@ -63,8 +63,9 @@ typedef enum {
     SJ_ERR_OOM = -2,        /* device allocation failed                            */
     SJ_ERR_GRID_COVER = -3, /* an MBB is not inside the closed grid box            */
     SJ_ERR_CUDA = -4,       /* a CUDA call failed (message in sj_last_error)       */
-    SJ_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                       */
-    SJ_ERR_BUSY = -6        /* resource in use                                     */
+    SJ_ERR_TIMEOUT = -5,    /* a bounded wait gave up (sj_server_wait_for)         */
+    SJ_ERR_BUSY = -6,       /* resource in use, or a request refused (admission)   */
+    SJ_ERR_CANCELLED = -7   /* the request was cancelled before it ran             */
 } sj_status;
 
 /* Refinement arithmetic. */
@@ -344,6 +345,32 @@ sj_status sj_engine_destroy(sj_engine *engine);
 #define SJ_NOALLOC_MAX_CELLS 1048576
 sj_status sj_p2p_join_noalloc(const sj_layer *layer, const double *pts, int64_t N, int32_t *out_id, double *out_d,
                               const sj_opts *opts, void *stream);
+
+/* Host-side fault injection, for tests of the failure paths (the paper has
+ * no counterpart).  Nothing here touches a GPU: a fault makes a host-side
+ * call report the failure it would report for real.
+ *   SJ_FAULT_ALLOC  device allocations of the library (layer builds, join
+ *                   scratch, engine workspaces, server arenas) fail as out of
+ *                   memory: the call returns SJ_ERR_OOM, frees what it had
+ *                   allocated and leaves its outputs and the layer untouched;
+ *   SJ_FAULT_ADMIT  sj_server_submit refuses the request with SJ_ERR_BUSY (as
+ *                   a full server would); the server keeps serving.
+ * After `after` calls that would trigger it succeed, the next `count` fail;
+ * count 0 (or SJ_FAULT_NONE) disarms.  Process-wide, thread-safe. */
+enum { SJ_FAULT_NONE = 0, SJ_FAULT_ALLOC = 1, SJ_FAULT_ADMIT = 2 };
+sj_status sj_fault_inject(int32_t kind, int32_t after, int32_t count);
+/* Failures still armed (0 when disarmed). */
+int32_t sj_fault_pending(void);
+
+/* 1 in a bounds-checked build of the library, else 0.  A checked build
+ * (paper_1403_0802_gb300.build.build(checked=True), compiled with
+ * -DSJ_CHECK_BOUNDS) tests the index of the kernels' main indexed accesses
+ * (point gathers, list records, counters, slots, results) before each access;
+ * an out-of-range access is skipped and recorded in an error word, and the
+ * join then returns SJ_ERR_CUDA ("bounds check: ...") after synchronising its
+ * stream.  No guard traps: the context stays usable.  Normal builds compile
+ * the guards away. */
+int32_t sj_bounds_checked(void);
 
 /* Message of the last failing call on this thread ("" if none). */
 const char *sj_last_error(void);

@@ -87,15 +87,29 @@ sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opts *opts, in
 /* Queue a request (thread-safe, does not block on the GPU).  *ticket receives
  * its id for sj_server_wait / sj_server_poll.  Errors: SJ_ERR_INVALID (bad
  * kind, missing layer, n out of range, NULL buffers, a request larger than
- * the device budget, a window outside [0, D] or on a PIP request), or the
- * error that stopped the worker. */
+ * the device budget, a window outside [0, D] or on a PIP request),
+ * SJ_ERR_BUSY (refused at admission; the server keeps serving), or the error
+ * that stopped the worker. */
 sj_status sj_server_submit(sj_server *s, const sj_serve_request *req, int64_t *ticket);
 
 /* Block until request `ticket` is done; *latency_s (may be NULL) receives
  * (results in host memory) - (arrival), in seconds, where arrival is the later
- * of submission and not_before.  Returns the status of the request (SJ_OK, or
- * the CUDA / engine error that failed it). */
+ * of submission and not_before.  Returns the status of the request (SJ_OK,
+ * SJ_ERR_CANCELLED, or the CUDA / engine error that failed it). */
 sj_status sj_server_wait(sj_server *s, int64_t ticket, double *latency_s);
+
+/* sj_server_wait with a deadline: SJ_ERR_TIMEOUT when the request is not done
+ * within timeout_s seconds (it keeps its place; wait for it again), else as
+ * sj_server_wait.  Errors: SJ_ERR_INVALID (unknown ticket, negative or NaN
+ * timeout), SJ_ERR_TIMEOUT, SJ_ERR_CANCELLED, the request's own error. */
+sj_status sj_server_wait_for(sj_server *s, int64_t ticket, double timeout_s, double *latency_s);
+
+/* Cancel a request that has not been admitted yet (it is queued, or its
+ * not_before lies ahead): the worker drops it before any device work, and its
+ * wait returns SJ_ERR_CANCELLED (its outputs untouched).  SJ_ERR_BUSY when the
+ * request is already admitted, running or done; SJ_ERR_INVALID for an unknown
+ * ticket. */
+sj_status sj_server_cancel(sj_server *s, int64_t ticket);
 
 /* Non-blocking: *done = 1 when request `ticket` is done, else 0. */
 sj_status sj_server_poll(sj_server *s, int64_t ticket, int32_t *done);

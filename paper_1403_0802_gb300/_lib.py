@@ -59,6 +59,8 @@ class sj_server_stats(C.Structure):
 
 
 SJ_OK, SJ_ERR_INVALID, SJ_ERR_OOM, SJ_ERR_GRID_COVER, SJ_ERR_CUDA, SJ_ERR_TIMEOUT, SJ_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6
+SJ_ERR_CANCELLED = -7
+SJ_FAULT_NONE, SJ_FAULT_ALLOC, SJ_FAULT_ADMIT = 0, 1, 2
 SJ_FP64, SJ_FP32X = 0, 1
 SJ_PER_REQUEST, SJ_PERSISTENT = 0, 1
 SJ_FLAG_TIME_REFINE = 1
@@ -97,6 +99,11 @@ SIGNATURES = {
     "sj_server_create": (C.c_int, [_P, _P, C.POINTER(sj_opts), _I32, _I64, _I64, _I32, _LP]),
     "sj_server_submit": (C.c_int, [_P, C.POINTER(sj_serve_request), C.POINTER(C.c_int64)]),
     "sj_server_wait": (C.c_int, [_P, _I64, C.POINTER(C.c_double)]),
+    "sj_server_wait_for": (C.c_int, [_P, _I64, _D, C.POINTER(C.c_double)]),
+    "sj_server_cancel": (C.c_int, [_P, _I64]),
+    "sj_fault_inject": (C.c_int, [_I32, _I32, _I32]),
+    "sj_fault_pending": (C.c_int32, []),
+    "sj_bounds_checked": (C.c_int32, []),
     "sj_server_poll": (C.c_int, [_P, _I64, C.POINTER(C.c_int32)]),
     "sj_server_drain": (C.c_int, [_P]),
     "sj_server_set_mode": (C.c_int, [_P, _I32, _I32]),
@@ -111,6 +118,16 @@ class SJError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str):
         super().__init__(f"{where}: status {status}: {msg}")
         self.status = status
+
+
+def use(path: str):
+    """Load the library from `path` (for example the bounds-checked build)
+    instead of the default one; only before the first call."""
+    global SO
+    with _lock:
+        if _lib is not None and path != SO:
+            raise RuntimeError("libsj.so is already loaded from " + SO)
+        SO = path
 
 
 def lib():

@@ -69,6 +69,74 @@ sj_status sj::cuda_fail(cudaError_t e, const char *what) {
                 std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// ------------------------------------------------------------------ bounds-checked build
+
+// After a join of a build compiled with SJ_CHECK_BOUNDS: synchronise the
+// stream and read the kernels' error words; a guard that fired (an index out
+// of range, skipped on the device) makes the call fail with SJ_ERR_CUDA.  In
+// normal builds: nothing.
+static sj_status check_bounds(cudaStream_t s) {
+#ifdef SJ_CHECK_BOUNDS
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const unsigned v = bounds_take_filter() | bounds_take_p2p() | bounds_take_pip();
+    if (v) return fail(SJ_ERR_CUDA, "bounds check: out-of-range device accesses skipped, guard codes " +
+                                        std::to_string(v));
+#else
+    (void)s;
+#endif
+    return SJ_OK;
+}
+
+extern "C" int32_t sj_bounds_checked(void) {
+#ifdef SJ_CHECK_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+// ------------------------------------------------------------------ fault injection
+
+static std::mutex g_fault_mu;
+static int g_fault_kind = SJ_FAULT_NONE, g_fault_after = 0, g_fault_count = 0;
+
+bool sj::fault_fires(int kind) {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    if (g_fault_kind != kind || g_fault_count <= 0) return false;
+    if (g_fault_after > 0) {
+        --g_fault_after;
+        return false;
+    }
+    if (--g_fault_count == 0) g_fault_kind = SJ_FAULT_NONE;
+    return true;
+}
+
+cudaError_t sj::dev_malloc(void **p, size_t bytes) {
+    if (fault_fires(SJ_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t sj::dev_malloc_async(void **p, size_t bytes, cudaStream_t s) {
+    if (fault_fires(SJ_FAULT_ALLOC)) return cudaErrorMemoryAllocation;
+    return cudaMallocAsync(p, bytes, s);
+}
+
+extern "C" sj_status sj_fault_inject(int32_t kind, int32_t after, int32_t count) {
+    if (kind != SJ_FAULT_NONE && kind != SJ_FAULT_ALLOC && kind != SJ_FAULT_ADMIT)
+        return fail(SJ_ERR_INVALID, "unknown fault kind");
+    if (after < 0 || count < 0) return fail(SJ_ERR_INVALID, "after and count must be >= 0");
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    g_fault_kind = count > 0 ? kind : SJ_FAULT_NONE;
+    g_fault_after = after;
+    g_fault_count = count;
+    return SJ_OK;
+}
+
+extern "C" int32_t sj_fault_pending(void) {
+    std::lock_guard<std::mutex> lk(g_fault_mu);
+    return g_fault_kind == SJ_FAULT_NONE ? 0 : g_fault_count;
+}
+
 // ------------------------------------------------------------------ device info
 
 static DevInfo g_dev[64];
@@ -123,11 +191,11 @@ static GridDev make_grid(const sj_grid *g) {
 // Threshold tables of point_cell for the grid of layer L (computed on the GPU
 // with the FP64 cell rule itself).
 static sj_status layer_tables(sj_layer *L, cudaStream_t s) {
-    CUDA_TRY(cudaMalloc((void **)&L->cell_keys, sizeof(unsigned long long) * ((size_t)L->g.nx + L->g.ny + 2)));
+    CUDA_TRY(dev_malloc((void **)&L->cell_keys, sizeof(unsigned long long) * ((size_t)L->g.nx + L->g.ny + 2)));
     CUDA_TRY(launch_thresholds(L->g, L->cell_keys, L->cell_keys + L->g.nx + 1, s));
     L->g.kx = L->cell_keys;
     L->g.ky = L->cell_keys + L->g.nx + 1;
-    CUDA_TRY(cudaMalloc((void **)&L->frames, sizeof(float) * ((size_t)L->g.nx + L->g.ny)));
+    CUDA_TRY(dev_malloc((void **)&L->frames, sizeof(float) * ((size_t)L->g.nx + L->g.ny)));
     CUDA_TRY(launch_frames(L->g, L->frames, L->frames + L->g.nx, s));
     L->xmax = std::max(std::max(std::fabs(L->grid.x0), std::fabs(L->grid.x1)),
                        std::max(std::fabs(L->grid.y0), std::fabs(L->grid.y1)));
@@ -223,7 +291,7 @@ struct LayerGuard {
 
 template <class T>
 static cudaError_t dalloc(T **p, size_t n) {
-    return cudaMalloc((void **)p, (n ? n : 1) * sizeof(T));
+    return dev_malloc((void **)p, (n ? n : 1) * sizeof(T));
 }
 
 static sj_status read_flag(int *dflag, cudaStream_t s, int *out) {
@@ -848,7 +916,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     const int ch_min = split ? std::min(ch, 8) : ch;
     size_t bytes = measure([&](Scratch &sc) { carve(sc, b, N, G, ch, need_fb, false, res, lS, ch_min); });
     Scratch sc;
-    CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
+    CUDA_TRY(dev_malloc_async((void **)&sc.base, bytes, s));
     carve(sc, b, N, G, ch, need_fb, false, res, lS, ch_min);
     cudaError_t e = cudaMemsetAsync(b.cnt, 0, sizeof(int) * (((size_t)G << lS) + 1), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b.totals, 0, sizeof(int) * 4, s);
@@ -909,6 +977,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     ra.spts = b.spts;
     ra.pts = (const double2 *)pts;
     ra.ch = ch;
+    ra.npts = (int)N;
     ra.cell_work = ba.cell_work;
     ra.budget = ba.budget;
     ra.res_id = b.res_id;   // cell-ordered results, every slot of a refined cell written
@@ -945,7 +1014,7 @@ static sj_status join_impl(const sj_layer *L, int kind, const double *pts, int64
     cudaError_t e2 = cudaFreeAsync(sc.base, s);
     if (e != cudaSuccess) return cuda_fail(e, "join launch");
     if (e2 != cudaSuccess) return cuda_fail(e2, "cudaFreeAsync");
-    return SJ_OK;
+    return check_bounds(s);
 }
 
 extern "C" sj_status sj_pip_join(const sj_layer *L, const double *pts, int64_t N, int32_t *out_id, const sj_opts *o,
@@ -1001,7 +1070,7 @@ static sj_status join_host(const sj_layer *L, int kind, const double *pts, int64
     }
     char *d = nullptr;
     size_t bp = (size_t)N * 16, bi = ((size_t)N * 4 + 255) & ~(size_t)255, bd = out_d ? (size_t)N * 8 : 0;
-    CUDA_TRY(cudaMallocAsync((void **)&d, bp + bi + bd, s));
+    CUDA_TRY(dev_malloc_async((void **)&d, bp + bi + bd, s));
     double *dp = (double *)d;
     int32_t *dI = (int32_t *)(d + bp);
     double *dD = out_d ? (double *)(d + bp + bi) : nullptr;
@@ -1083,7 +1152,7 @@ extern "C" sj_status sj_bucket_points(const double *pts, int64_t N, const sj_gri
     int2 *kr, *bs;
     unsigned long long *keys;
     size_t bytes = measure([&](Scratch &x) { lay(x, &cnt, &totals, &kr, &bs, &keys); });
-    CUDA_TRY(cudaMallocAsync((void **)&sc.base, bytes, s));
+    CUDA_TRY(dev_malloc_async((void **)&sc.base, bytes, s));
     lay(sc, &cnt, &totals, &kr, &bs, &keys);
     gd.kx = keys;
     gd.ky = keys + gd.nx + 1;
@@ -1117,7 +1186,7 @@ extern "C" sj_status sj_pip_census(const sj_layer *L, const double *pts, int64_t
     if (N == 0) return SJ_OK;
     cudaStream_t s = (cudaStream_t)stream;
     unsigned long long *d = nullptr, h[2] = {0, 0};
-    CUDA_TRY(cudaMallocAsync((void **)&d, sizeof(h), s));
+    CUDA_TRY(dev_malloc_async((void **)&d, sizeof(h), s));
     RefineArgs ra{};
     fill_refine(L, ra);
     cudaError_t e = cudaMemsetAsync(d, 0, sizeof(h), s);
@@ -1252,6 +1321,7 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     ra.perm = b.perm;
     ra.spts = b.spts;
     ra.ch = NOALLOC_CH;
+    ra.npts = (int)N;
     ra.out_id = out_id;
     ra.out_d = out_d;
     ra.fb = b.fb;
@@ -1261,5 +1331,5 @@ extern "C" sj_status sj_p2p_join_noalloc(const sj_layer *L, const double *pts, i
     ra.claim = (N >= 2LL * NOALLOC_CH * (long long)G) ? 2 : 1;
     CUDA_TRY(launch_p2p_refine(ra, form, 4, di->sms * di->p2p_bps[form], s));
     if (need_fb) CUDA_TRY(launch_p2p_recheck(ra, di->sms * 4, s));
-    return SJ_OK;
+    return check_bounds(s);
 }

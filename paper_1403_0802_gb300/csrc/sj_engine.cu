@@ -190,7 +190,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
         w->d_meta = x.take<int>(4);
     };
     size_t bytes = measure(lay);
-    CUDA_TRY(cudaMalloc((void **)&w->base, bytes));
+    CUDA_TRY(dev_malloc((void **)&w->base, bytes));
     Scratch sc;
     sc.base = w->base;
     lay(sc);
@@ -220,6 +220,7 @@ static sj_status work_create(sj_engine *E, const sj_layer *L, LayerWork **out) {
     ra.perm = perm;
     ra.spts = spts;
     ra.ch = E->ch;
+    ra.npts = (int)E->max_points;   // slots and point indices of a round stay below it
     ra.res_id = res_id;
     ra.res_d = res_d;
     ra.fb = fb;

@@ -11,6 +11,8 @@
 
 namespace sj {
 
+unsigned bounds_take_filter() { return bounds_take(); }
+
 // ------------------------------------------------------------------ block scan helpers
 
 constexpr int SCAN_T = 256;
@@ -219,7 +221,7 @@ __global__ void k_cell_hist(BucketArgs a) {
                         r[u] = 1;
                     }
                 }
-                if (c[u] < sentinel) r[u] = atomicAdd(&a.cnt[c[u]], 1);
+                if (c[u] < sentinel && SJ_IN_BOUNDS(c[u] >= 0, BND_BUCKET)) r[u] = atomicAdd(&a.cnt[c[u]], 1);
             }
         }
 #pragma unroll
@@ -335,7 +337,7 @@ __global__ void k_scatter(BucketArgs a) {
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            if (pos[u] >= 0) {
+            if (pos[u] >= 0 && SJ_IN_BOUNDS(pos[u] < a.n, BND_SCATTER)) {
                 a.perm[pos[u]] = (int)(i0 + u * T);
                 if (a.spts) a.spts[pos[u]] = p[u];
             }
@@ -362,6 +364,7 @@ __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d,
         for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < (unsigned)n) ? pos[i0 + u * T] : -1;
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
+            if (j[u] >= 0 && !SJ_IN_BOUNDS(j[u] < n, BND_UNSORT)) j[u] = -1;
             id[u] = j[u] >= 0 ? res_id[j[u]] : -1;
             if (out_d) d[u] = j[u] >= 0 ? res_d[j[u]] : inf;
         }
@@ -403,8 +406,10 @@ __global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, d
 #pragma unroll
         for (int u = 0; u < UNR; ++u) j[u] = (i0 + u * T < (unsigned)n) ? pos[i0 + u * T] : -1;
 #pragma unroll
-        for (int u = 0; u < UNR; ++u)
+        for (int u = 0; u < UNR; ++u) {
+            if (j[u] >= 0 && !SJ_IN_BOUNDS(j[u] < n, BND_UNSORT)) j[u] = -1;
             if (j[u] >= 0) r[u] = res[j[u]];
+        }
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const unsigned i = i0 + u * T;

@@ -100,6 +100,14 @@ struct DevInfo {
 
 sj_status fail(sj_status st, const std::string &msg);
 sj_status cuda_fail(cudaError_t e, const char *what);
+
+// Host-side fault injection (sj_fault_inject): true when an armed fault of
+// this kind fires now.
+bool fault_fires(int kind);
+// Device allocations of the library, which an armed SJ_FAULT_ALLOC makes fail
+// as out of memory.
+cudaError_t dev_malloc(void **p, size_t bytes);
+cudaError_t dev_malloc_async(void **p, size_t bytes, cudaStream_t s);
 sj_status device_info(int dev, DevInfo **out);
 void fill_refine(const sj_layer *L, RefineArgs &ra);
 

@@ -141,6 +141,30 @@ __device__ __forceinline__ float2 cell_frame(const float *fx, const float *fy, i
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 
+// Bounds-checked builds (compiled with -DSJ_CHECK_BOUNDS): a guarded access
+// first tests its index; out of range, it is skipped and the guard's code is
+// OR-ed into this translation unit's error word, which the host reads back
+// after the call (bounds_take()) -- no trap, the context stays usable.  In
+// normal builds a guard is `true` and costs nothing.
+enum {
+    BND_BUCKET = 1, BND_SCATTER = 2, BND_UNSORT = 4, BND_P2P_POINT = 8, BND_P2P_REC = 16, BND_P2P_RES = 32,
+    BND_PIP_POINT = 64, BND_PIP_REC = 128, BND_PIP_RES = 256
+};
+#ifdef SJ_CHECK_BOUNDS
+static __device__ unsigned g_bounds_err;
+#define SJ_IN_BOUNDS(cond, code) ((cond) || (atomicOr(&g_bounds_err, (unsigned)(code)), false))
+// This translation unit's error word, read and cleared (host).
+static inline unsigned bounds_take() {
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_err, sizeof(v)) != cudaSuccess) return 0x80000000u;
+    cudaMemcpyToSymbol(g_bounds_err, &z, sizeof(z));
+    return v;
+}
+#else
+#define SJ_IN_BOUNDS(cond, code) true
+static inline unsigned bounds_take() { return 0; }
+#endif
+
 // 16-byte asynchronous copy global -> shared (cp.async, cached in L1); both
 // addresses 16-byte aligned.  The copying thread sees the data after
 // copy_async_wait_all().
@@ -271,6 +295,7 @@ struct RefineArgs {
     float eps_abs;           // absolute term of the split-coordinate rounding bound
     const float *frame_x;    // [nx] FP32 cell frame origins along x
     const float *frame_y;    // [ny]
+    int npts;                // input points (slot indices and perm values stay below it)
     int ch;                  // points per work item (at most; see cell_chunk)
     const int *cell_work;    // [G] per-point edge / segment work of each cell (or null)
     int budget;              // edge budget per point of an item (0: none)
@@ -322,6 +347,12 @@ cudaError_t launch_cell_result(const int *cand_start, const int *cand_ids, const
 cudaError_t launch_pip_classify(const GridDev &g, const int *cand_start, const int *cand_ids, const int *prow_base,
                                 const int *prow_r0, const int *prow_start, const int *pedge_ids, const int *nxt,
                                 const double2 *verts, double delta, unsigned char *cls, cudaStream_t s);
+
+// The error words of the bounds-checked build, per translation unit, read
+// and cleared (0 in normal builds).
+unsigned bounds_take_filter();
+unsigned bounds_take_p2p();
+unsigned bounds_take_pip();
 
 // Host-side launchers (defined in the .cu files).
 cudaError_t launch_pip_refine(const RefineArgs &a, int form, int warps_per_block, int blocks, cudaStream_t s);

@@ -48,6 +48,8 @@
 
 namespace sj {
 
+unsigned bounds_take_p2p() { return bounds_take(); }
+
 constexpr int P2P_WARPS = 4;
 
 struct alignas(16) Seg64 {
@@ -307,11 +309,13 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) k_p2p_refine(RefineArgs a) {
 #pragma unroll
             for (int u = 0; u < PQ; ++u) {
                 const int q = lane + 32 * u;
-                src[u] = q < np ? (a.spts ? j0 + q : a.perm[j0 + q]) : -1;
+                src[u] = (q < np && SJ_IN_BOUNDS(j0 + q < a.npts, BND_P2P_POINT)) ? (a.spts ? j0 + q : a.perm[j0 + q])
+                                                                                 : -1;
             }
 #pragma unroll
             for (int u = 0; u < PQ; ++u)
-                if (src[u] >= 0) copy16_async(pbuf + lane + 32 * u, a.spts ? a.spts + src[u] : a.pts + src[u]);
+                if (src[u] >= 0 && SJ_IN_BOUNDS(src[u] < a.npts, BND_P2P_POINT))
+                    copy16_async(pbuf + lane + 32 * u, a.spts ? a.spts + src[u] : a.pts + src[u]);
             copy_async_wait_all();
         }
         for (int q = lane; q < np; q += 32) {
@@ -350,7 +354,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) k_p2p_refine(RefineArgs a) {
             bool keep = false;
             int i = 0, sid = 0;
             float ax = 0.0f, ay = 0.0f, ex = 0.0f, ey = 0.0f, inv = 0.0f, smag = 0.0f;
-            if (g < g1) {
+            if (g < g1 && SJ_IN_BOUNDS(g < a.cseg_start[a.g.G], BND_P2P_REC)) {
                 const float4 r0 = a.cseg_rec[2 * (size_t)g], r1 = a.cseg_rec[2 * (size_t)g + 1];
                 ax = r0.x;
                 ay = r0.y;
@@ -451,6 +455,7 @@ __global__ void __launch_bounds__(NW * 32, 32 / NW) k_p2p_refine(RefineArgs a) {
                     }
                 }
             }
+            if (!SJ_IN_BOUNDS(j0 + q < a.npts, BND_P2P_RES)) continue;
             if (a.resf) {
                 a.resf[j0 + q] = ResF{out, df};
             } else if (a.resd) {

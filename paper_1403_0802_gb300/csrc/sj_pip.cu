@@ -43,6 +43,8 @@
 
 namespace sj {
 
+unsigned bounds_take_pip() { return bounds_take(); }
+
 constexpr int PIP_WARPS = 4;
 
 struct alignas(16) Edge64 {
@@ -276,7 +278,9 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
         // 1. points, the range of their FP32 y truncations and the smallest x truncation
         float ylo = FINF, yhi = -FINF, xlo = FINF;
         for (int q = lane; q < np; q += 32) {
-            const double2 p = slot_point(a, j0 + q);
+            double2 p = make_double2(0.0, 0.0);
+            if (SJ_IN_BOUNDS(j0 + q < a.npts && (a.spts || a.perm[j0 + q] < a.npts), BND_PIP_POINT))
+                p = slot_point(a, j0 + q);
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
@@ -364,7 +368,9 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
                     const int lo = key_bound(keys, n0, __fsub_rd(pyh, hj), false);
                     const int hi = key_bound(keys, n0, pyh, true);
                     unsigned par = 0;
-                    for (int t = lo; t < hi; ++t) par ^= (unsigned)near_edge_cross<FP32>(a, s, q, b0 + t, fo, c_fb);
+                    for (int t = lo; t < hi; ++t)
+                        if (SJ_IN_BOUNDS(b0 + t < a.bnear_start[a.cand_start[a.g.G]], BND_PIP_REC))
+                            par ^= (unsigned)near_edge_cross<FP32>(a, s, q, b0 + t, fo, c_fb);
                     c_wtests += (unsigned long long)(hi > lo ? hi - lo : 0);
                     if (par & 1u) s.par[q] ^= 1u << j;
                 }
@@ -399,7 +405,8 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
                 if (g < E) {
                     while (s.coff[kw + 1] <= g) ++kw;   // candidate of edge g (g grows by 32)
                     k = kw;
-                    const int e = s.cvb[kw] + (g - s.coff[kw]);
+                    int e = s.cvb[kw] + (g - s.coff[kw]);
+                    if (!SJ_IN_BOUNDS(e < a.bnear_start[a.cand_start[a.g.G]], BND_PIP_REC)) e = 0;
                     i = a.bnear_ids[e];
                     if constexpr (FP32) {
                         va = a.bnear_rec[2 * (size_t)e];
@@ -452,6 +459,7 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
         }
         for (int q = lane; q < np; q += 32) {
             const int f = s.found[q];
+            if (!SJ_IN_BOUNDS(j0 + q < a.npts, BND_PIP_RES)) continue;
             if (a.res_id) a.res_id[j0 + q] = f;
             else if (f >= 0) a.out_id[a.perm[j0 + q]] = f;
             if (f >= 0) ++c_hits;

@@ -99,6 +99,7 @@ struct Req {
     sj_serve_request r{};
     double t_submit = 0.0, t_done = 0.0;
     int state = Q_QUEUED;
+    bool cancel = false;     // sj_server_cancel asked; the worker finishes it before admission
     sj_status status = SJ_OK;
     Block *blk = nullptr;
     double *d_pts = nullptr;
@@ -141,6 +142,7 @@ struct sj_server {
     std::condition_variable cv_work, cv_done;
     std::deque<Req *> incoming;                       // submitted, not yet taken by the worker
     std::unordered_map<int64_t, Req *> reqs;          // every request not yet waited for
+    std::atomic<bool> cancels{false};                 // a cancel is pending (wakes the worker)
     int64_t next_ticket = 0;
     bool stop = false;
     sj_status fatal = SJ_OK;
@@ -158,6 +160,7 @@ struct sj_server {
     std::deque<CopyBatch *> batches;                  // admission batches, oldest first
 
     void run();
+    void finish_cancelled(std::deque<Req *> &d);
     bool admit();
     bool launch_round();
     bool retire();
@@ -192,6 +195,28 @@ void sj_server::fail_all(sj_status st, const std::string &msg) {
     in_flight.clear();
     incoming.clear();
     cv_done.notify_all();
+}
+
+// Requests cancelled before admission leave their queue, done with status
+// SJ_ERR_CANCELLED (worker thread).
+void sj_server::finish_cancelled(std::deque<Req *> &d) {
+    std::lock_guard<std::mutex> lk(mu);
+    bool any = false;
+    for (auto it = d.begin(); it != d.end();) {
+        Req *q = *it;
+        if (q->cancel) {
+            q->state = Q_DONE;
+            q->status = SJ_ERR_CANCELLED;
+            q->t_done = now();
+            completed++;
+            it = d.erase(it);
+            any = true;
+        } else {
+            ++it;
+        }
+    }
+    cancels = false;
+    if (any) cv_done.notify_all();
 }
 
 // Admission: arena blocks and host-to-device copies, in submission order.
@@ -376,7 +401,7 @@ void sj_server::run() {
                     const double dt = arriving.front()->t_submit - now();
                     if (dt > 2e-4)
                         cv_work.wait_for(lk, std::chrono::duration<double>(dt - 1e-4),
-                                         [&] { return stop || !incoming.empty(); });
+                                         [&] { return stop || cancels || !incoming.empty(); });
                 }
             }
             while (!incoming.empty()) {
@@ -387,6 +412,10 @@ void sj_server::run() {
         if (fatal != SJ_OK) {
             fail_all(fatal, fatal_msg);
             continue;
+        }
+        if (cancels) {
+            finish_cancelled(arriving);
+            finish_cancelled(queue);
         }
         const double t = now();
         while (!arriving.empty() && arriving.front()->t_submit <= t) {   // arrivals, in order
@@ -442,7 +471,7 @@ extern "C" sj_status sj_server_create(sj_layer *pip, sj_layer *p2p, const sj_opt
         delete S;
         return st;
     };
-    cudaError_t e = cudaMalloc((void **)&S->ring.base, (size_t)hbm_budget);
+    cudaError_t e = dev_malloc((void **)&S->ring.base, (size_t)hbm_budget);
     if (e != cudaSuccess) return undo(cuda_fail(e, "server arena"));
     S->ring.cap = (size_t)hbm_budget / ALIGN * ALIGN;
     for (cudaStream_t *st_ : {&S->copy_in, &S->compute, &S->copy_out}) {
@@ -512,6 +541,7 @@ extern "C" sj_status sj_server_submit(sj_server *S, const sj_serve_request *req,
     if (r.use_window && (r.kind != SJ_SERVE_P2P || !(r.window >= 0.0 && r.window <= S->layers[r.kind]->D)))
         return fail(SJ_ERR_INVALID, "a request window needs a P2P request and 0 <= window <= the layer's D");
     if (request_bytes(r) > S->ring.cap) return fail(SJ_ERR_INVALID, "request larger than the device budget");
+    if (fault_fires(SJ_FAULT_ADMIT)) return fail(SJ_ERR_BUSY, "request refused at admission (injected fault)");
     Req *q = new Req();
     q->r = r;
     if (r.kind == SJ_SERVE_PIP) q->r.out_d = nullptr;
@@ -543,7 +573,43 @@ extern "C" sj_status sj_server_wait(sj_server *S, int64_t ticket, double *latenc
     const sj_status st = q->status;
     S->reqs.erase(it);
     delete q;
+    if (st == SJ_ERR_CANCELLED) return fail(st, "request cancelled");
     if (st != SJ_OK) return fail(st, "request failed: " + S->fatal_msg);
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_server_wait_for(sj_server *S, int64_t ticket, double timeout_s, double *latency_s) {
+    if (!S) return fail(SJ_ERR_INVALID, "NULL server");
+    if (!(timeout_s >= 0.0)) return fail(SJ_ERR_INVALID, "timeout must be >= 0");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(SJ_ERR_INVALID, "unknown or already waited-for ticket");
+    Req *q = it->second;
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(std::min(timeout_s, 1e9)));
+    if (!S->cv_done.wait_until(lk, deadline, [&] { return q->state == Q_DONE; }))
+        return fail(SJ_ERR_TIMEOUT, "request not done within the timeout (it keeps running; wait again)");
+    if (latency_s) *latency_s = q->t_done - q->t_submit;
+    const sj_status st = q->status;
+    S->reqs.erase(it);
+    delete q;
+    if (st == SJ_ERR_CANCELLED) return fail(st, "request cancelled");
+    if (st != SJ_OK) return fail(st, "request failed: " + S->fatal_msg);
+    return SJ_OK;
+}
+
+extern "C" sj_status sj_server_cancel(sj_server *S, int64_t ticket) {
+    if (!S) return fail(SJ_ERR_INVALID, "NULL server");
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        auto it = S->reqs.find(ticket);
+        if (it == S->reqs.end()) return fail(SJ_ERR_INVALID, "unknown or already waited-for ticket");
+        Req *q = it->second;
+        if (q->state != Q_QUEUED) return fail(SJ_ERR_BUSY, "request already admitted or done");
+        q->cancel = true;
+        S->cancels = true;
+    }
+    S->cv_work.notify_one();
     return SJ_OK;
 }
 

@@ -134,3 +134,23 @@ def test_server_struct_layouts_and_argument_checks(libsj):
     t = C.c_int64()
     assert lib.sj_server_submit(None, None, C.byref(t)) == _lib.SJ_ERR_INVALID
     assert lib.sj_server_destroy(None) == _lib.SJ_OK
+
+
+def test_fault_injection_and_checked_build_without_gpu(libsj):
+    """The fault hook is host-side state (armed, counted, disarmed without a
+    GPU); server calls check their arguments first; the bounds-checked build
+    says so, the normal build does not."""
+    from paper_1403_0802_gb300 import _lib, build
+    lib = _lib.lib()
+    assert lib.sj_fault_inject(7, 0, 1) == _lib.SJ_ERR_INVALID
+    assert lib.sj_fault_inject(_lib.SJ_FAULT_ALLOC, -1, 1) == _lib.SJ_ERR_INVALID
+    assert lib.sj_fault_inject(_lib.SJ_FAULT_ALLOC, 2, 3) == _lib.SJ_OK
+    assert lib.sj_fault_pending() == 3
+    assert lib.sj_fault_inject(_lib.SJ_FAULT_NONE, 0, 0) == _lib.SJ_OK
+    assert lib.sj_fault_pending() == 0
+    assert lib.sj_server_cancel(None, 0) == _lib.SJ_ERR_INVALID
+    assert lib.sj_server_wait_for(None, 0, 1.0, None) == _lib.SJ_ERR_INVALID
+    assert lib.sj_bounds_checked() == 0
+    checked = C.CDLL(build.build(checked=True))
+    checked.sj_bounds_checked.restype = C.c_int32
+    assert checked.sj_bounds_checked() == 1

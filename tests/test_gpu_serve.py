@@ -141,3 +141,48 @@ def test_admission_waits_for_device_memory(server):
                 check_p2p_request(api, srv, r, srv.form)
     finally:
         tight.close()
+
+
+def test_admission_refusal_cancellation_and_deadline(server):
+    """Injected admission refusal (the server keeps serving), a request
+    cancelled before it is admitted (its wait reports SJ_ERR_CANCELLED and its
+    outputs stay untouched), and a wait with a deadline that gives up
+    (SJ_ERR_TIMEOUT) on a request still ahead, then completes it."""
+    api, serve, srv, pool_p, pool_l = server
+    import ctypes as C
+    from paper_1403_0802_gb300 import _lib as L
+    lib = L.lib()
+    pts = pool_p[:2000].contiguous()
+    outs = [torch.full((2000,), 7, dtype=torch.int32, pin_memory=True) for _ in range(4)]
+    tk, lat = C.c_int64(), C.c_double()
+
+    def req(k, delay):
+        r = L.sj_serve_request(L.SJ_SERVE_PIP, 0, pts.data_ptr(), 2000, outs[k].data_ptr(), None, 0.0)
+        r.not_before = lib.sj_server_now(srv.handle) + delay
+        return r
+
+    want = api.pip_join(srv.layers[serve.PIP], pts.cuda(), form=srv.form).cpu()
+    assert lib.sj_fault_inject(L.SJ_FAULT_ADMIT, 1, 1) == L.SJ_OK
+    r0 = req(0, 0.0)
+    L.check(lib.sj_server_submit(srv.handle, C.byref(r0), C.byref(tk)), "submit")
+    t0 = tk.value
+    r1 = req(1, 0.0)
+    assert lib.sj_server_submit(srv.handle, C.byref(r1), C.byref(tk)) == L.SJ_ERR_BUSY
+    L.check(lib.sj_server_wait(srv.handle, t0, C.byref(lat)), "wait")
+    assert torch.equal(outs[0], want) and bool((outs[1] == 7).all())
+    # cancelled before admission (arrives in 0.5 s)
+    r2 = req(2, 0.5)
+    L.check(lib.sj_server_submit(srv.handle, C.byref(r2), C.byref(tk)), "submit")
+    t2 = tk.value
+    assert lib.sj_server_cancel(srv.handle, t2) == L.SJ_OK
+    assert lib.sj_server_wait(srv.handle, t2, C.byref(lat)) == L.SJ_ERR_CANCELLED
+    assert bool((outs[2] == 7).all())
+    # a deadline that runs out, then the request completes
+    r3 = req(3, 0.3)
+    L.check(lib.sj_server_submit(srv.handle, C.byref(r3), C.byref(tk)), "submit")
+    t3 = tk.value
+    assert lib.sj_server_wait_for(srv.handle, t3, 0.01, C.byref(lat)) == L.SJ_ERR_TIMEOUT
+    assert lib.sj_server_cancel(srv.handle, 10 ** 9) == L.SJ_ERR_INVALID
+    L.check(lib.sj_server_wait_for(srv.handle, t3, 10.0, C.byref(lat)), "wait_for")
+    assert torch.equal(outs[3], want)
+    assert lib.sj_server_cancel(srv.handle, t3) == L.SJ_ERR_INVALID     # already waited for
