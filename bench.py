@@ -21,9 +21,12 @@ region, as in serving; that build time is reported as config.layer_build_ms.
 The default run (the P2P workload at one GPU) prints ONE JSON line: the P2P
 headline, plus the other halves of the metric as extra keys, each timed the
 same way (CUDA events on the join's stream, its own clock record, roofline,
-CPU baseline and plain FP64 comparison): "pip_stars" (the PIP workload),
-"pip_at_scale_layer2" (100 M points against the heavy-tail tiling) and
-"serve" (the serving workload); --no-extra leaves them out.
+CPU baseline with the GPU's measured error against the oracle, and plain FP64
+comparison): "pip_stars" (the PIP workload), "pip_at_scale_layer1" and
+"pip_at_scale_layer2" (100 M points against the 40,000-tile and the
+heavy-tail tilings), "p2p_at_scale_D50" / "_D100" / "_D200" (170 M points,
+150,000 walks) and "serve" (the serving workload); --no-extra leaves them
+out.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload ...] [--form fp32x|fp64]
@@ -647,12 +650,23 @@ def run_ours(args):
         extra["pip_stars"] = join_leg(api, a1, ws, dev, stream, 1, sub_steps(0.12, args.steps), 3, peaks,
                                       baselines=not args.no_baselines)
         del ws
-        a2 = copy.copy(args)
-        a2.workload, a2.layer, a2.ppi = "pip3", 2, 0
-        wt = workload(a2)
-        extra["pip_at_scale_layer2"] = join_leg(api, a2, wt, dev, stream, 1, sub_steps(9.7, args.steps), 3, peaks,
-                                                baselines=not args.no_baselines)
-        del wt
+        for layer in (1, 2):      # the PIP-at-scale layers (the same 100 M points)
+            a2 = copy.copy(args)
+            a2.workload, a2.layer, a2.ppi = "pip3", layer, 0
+            wt = workload(a2)
+            extra[f"pip_at_scale_layer{layer}"] = join_leg(api, a2, wt, dev, stream, 1, sub_steps(7.0, args.steps),
+                                                           3, peaks, baselines=not args.no_baselines)
+            del wt
+        a4 = copy.copy(args)
+        a4.workload, a4.ppi = "p2p4", 0
+        w4 = workload(a4)
+        base_name = w4.name
+        for D in (50.0, 100.0, 200.0):   # P2P at scale: one layer per window, the same 170 M points
+            w4.D = D
+            w4.name = base_name.replace("_D100_", f"_D{int(D)}_")
+            extra[f"p2p_at_scale_D{int(D)}"] = join_leg(api, a4, w4, dev, stream, 1, sub_steps(15.0, args.steps), 3,
+                                                        peaks, baselines=not args.no_baselines)
+        del w4
         extra["serve"] = serve_leg(args)
     if rank == 0:
         line = {

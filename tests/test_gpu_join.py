@@ -630,46 +630,65 @@ def test_pip_tiles_subset(api, oracle, form, layer):
 SAMPLE = 200_000
 
 
+@pytest.fixture(scope="module")
+def tiles_points():
+    """The 100,000,000 clustered points of the PIP-at-scale workloads (the
+    same points for every layer), generated once for the module."""
+    return synth.pip_tiles(layer=1).points
+
+
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("layer", [1, 2, 3])
-def test_pip_at_scale_full_size_sampled(api, oracle, layer):
+def test_pip_at_scale_full_size_sampled(api, oracle, tiles_points, layer, form):
     """100,000,000 clustered points against the 40,000-tile (layer 1), the
     heavy-tail 14,000-tile (layer 2) or the multi-ring (layer 3: layer 1 with
-    island holes) tiling, grid 1024 x 1024, FP32X: ids of a 200,000-point
-    sample bit-identical to the oracle; every point in exactly one polygon."""
-    w = synth.pip_tiles(layer=layer)
+    island holes) tiling, grid 1024 x 1024, in both forms with the launch
+    settings the benchmark uses: ids of a 200,000-point sample bit-identical
+    to the oracle; every point in exactly one polygon."""
+    import bench
+    w = synth.pip_tiles(n_points=1, layer=layer)
     P = w.polygons
+    t = bench.TUNED[f"pip3_{layer}"]
     with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, w.grid) as layer_:
-        pts = torch.as_tensor(w.points, device="cuda")
-        got = api.pip_join(layer_, pts, form="fp32x")
+        pts = torch.as_tensor(tiles_points, device="cuda")
+        got = api.pip_join(layer_, pts, form=form, pts_per_item=t["ppi"], block=t["block"],
+                           edges_per_chunk=t["edges"])
         del pts
         got = to_np(got)
     assert (got >= 0).all()                              # a tiling covers the extent
-    idx = np.random.default_rng(layer).choice(len(w.points), SAMPLE, replace=False)
-    ref = oracle.pip_join(w.grid, np.ascontiguousarray(w.points[idx]), P.verts, P.ring_off, P.poly_ring_off)
+    idx = np.random.default_rng(layer).choice(len(tiles_points), SAMPLE, replace=False)
+    ref = oracle.pip_join(w.grid, np.ascontiguousarray(tiles_points[idx]), P.verts, P.ring_off, P.poly_ring_off)
     np.testing.assert_array_equal(got[idx], ref)
     if layer == 3:                                       # points in holes answer the island
         assert (ref >= 40_000).sum() > 1000
 
 
-def test_p2p_at_scale_full_size_sampled(api, oracle):
+@pytest.fixture(scope="module")
+def walks_at_scale():
+    """The P2P-at-scale workload (170,000,000 clustered points, 150,000
+    lognormal walks), generated once for the module; D varies per test."""
+    return synth.p2p_walks_lognormal()
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("D", [50.0, 100.0, 200.0])
+def test_p2p_at_scale_full_size_sampled(api, oracle, walks_at_scale, D, form):
     """170,000,000 clustered points against 150,000 lognormal random walks,
-    D = 100 m, grid 512 x 512, FP32X: a 200,000-point sample against the
-    oracle (ids exact up to near-ties, distances within the certified bound)."""
-    w = synth.p2p_walks_lognormal()
+    grid 512 x 512, D = 50, 100 and 200 m, both forms: a 200,000-point sample
+    against the oracle (ids exact up to near-ties, FP64 distances within
+    1e-12 relative, FP32X within the certified bound)."""
+    w = walks_at_scale
     Lw = w.polylines
-    with api.p2p_layer(Lw.verts, Lw.line_off, w.D, w.grid) as layer:
+    with api.p2p_layer(Lw.verts, Lw.line_off, D, w.grid) as layer:
         pts = torch.as_tensor(w.points, device="cuda")
-        gid, gd = api.p2p_join(layer, pts, form="fp32x")
+        gid, gd = api.p2p_join(layer, pts, form=form)
         del pts
         gid, gd = to_np(gid), to_np(gd)
     idx = np.random.default_rng(4).choice(len(w.points), SAMPLE, replace=False)
-
-    class W:
-        pass
-    s = W()
-    s.grid, s.points, s.D, s.polylines = w.grid, np.ascontiguousarray(w.points[idx]), w.D, Lw
-    r = check_p2p(oracle, s, gid[idx], gd[idx], "fp32x")
-    assert 0.05 < r["hit_frac"] < 1.0
+    sample = np.ascontiguousarray(w.points[idx])
+    ref = P2PRef(oracle, w.grid, Lw.verts, Lw.line_off, D)
+    r = ref.check(sample, gid[idx], gd[idx], form)
+    assert 0.02 < r["hit_frac"] < 1.0
 
 
 def test_pip_at_the_maximum_point_count(api, oracle):

@@ -186,3 +186,40 @@ def test_admission_refusal_cancellation_and_deadline(server):
     L.check(lib.sj_server_wait_for(srv.handle, t3, 10.0, C.byref(lat)), "wait_for")
     assert torch.equal(outs[3], want)
     assert lib.sj_server_cancel(srv.handle, t3) == L.SJ_ERR_INVALID     # already waited for
+
+
+def test_serving_on_the_full_layers(oracle):
+    """The serving workload's layers (40,000 tiles; 150,000 lognormal walks,
+    D = 100 m), requests of 100 k - 3 M points arriving while others run,
+    batched rounds of up to 6 M points: every request checked against the
+    oracle on a seeded 20,000-point sample of its points (PIP ids bit for bit;
+    P2P with the parity bar)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1403_0802_gb300 import api, build, serve
+    build.build()
+    wp = synth.pip_tiles(n_points=8_000_000, layer=1)
+    wl = synth.p2p_walks_lognormal(n_points=8_000_000, n_lines=150_000, D=100.0)
+    P, L = wp.polygons, wl.polylines
+    pref = PIPRef(oracle, wp.grid, P.verts, P.ring_off, P.poly_ring_off)
+    lref = P2PRef(oracle, wl.grid, L.verts, L.line_off, wl.D)
+    pool_p = torch.from_numpy(wp.points).pin_memory()
+    pool_l = torch.from_numpy(wl.points).pin_memory()
+    with api.pip_layer(P.verts, P.ring_off, P.poly_ring_off, wp.grid) as pip, \
+            api.p2p_layer(L.verts, L.line_off, wl.D, wl.grid) as p2p:
+        srv = serve.Server(pip, p2p, form="fp32x", round_points=6_000_000, max_requests=256)
+        try:
+            reqs = serve.make_stream(24, rate_per_s=40.0, pool_pip=pool_p, pool_p2p=pool_l, size_min=100_000,
+                                     size_max=3_000_000, seed=11)
+            stats = srv.run(reqs, mode="batched")
+        finally:
+            srv.close()
+    assert stats["requests"] == 24
+    rng = np.random.default_rng(12)
+    for r in reqs:
+        idx = np.sort(rng.choice(r.n, min(r.n, 20_000), replace=False))
+        pts = np.ascontiguousarray(r.pts.numpy()[idx])
+        if r.kind == serve.PIP:
+            np.testing.assert_array_equal(r.out_id.numpy()[idx], pref.join(pts))
+        else:
+            lref.check(pts, r.out_id.numpy()[idx], r.out_d.numpy()[idx], "fp32x")
