@@ -667,7 +667,7 @@ def run_ours(args):
             extra[f"p2p_at_scale_D{int(D)}"] = join_leg(api, a4, w4, dev, stream, 1, sub_steps(15.0, args.steps), 3,
                                                         peaks, baselines=not args.no_baselines)
         del w4
-        extra["serve"] = serve_leg(args)
+        extra["serve"] = serve_leg_child(args)
     if rank == 0:
         line = {
             "metric": metric_name(w.kind), "value": head["value"], "unit": "points/s", "n_gpus": world,
@@ -685,6 +685,20 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def serve_leg_child(args):
+    """The serving leg in a process of its own (python bench.py --workload
+    serve): the earlier legs leave host state behind -- multi-GB pinned
+    buffers, the oracle's host threads -- that slows a host-bound serving loop
+    run after them in the same process."""
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "serve", "--requests", str(args.requests),
+           "--form", args.form]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not lines:
+        return {"error": f"serving leg exited {r.returncode}: {r.stderr[-500:]}"}
+    return json.loads(lines[-1])
 
 
 def serve_leg(args):

@@ -9,14 +9,17 @@
  *   - admits queued requests in submission order while their device memory
  *     (points, ids, distances) fits a fixed device budget, and copies their
  *     points to the device on a copy stream;
- *   - whenever fewer than two rounds are in flight, forms a round from every
- *     admitted request (up to round_points points and max_requests requests)
- *     and runs it through the batched engine (sj_engine_round: one graph
- *     replay per layer, however many requests; a round of one request, or of
- *     fewer than min(10^6, round_points / 4) points, runs as direct join
- *     calls instead, which cost less than the graph sized for the largest
- *     round), so that requests arriving while a round runs join the next one
- *     (SJ_SERVE_BATCHED); or runs one
+ *   - whenever fewer than two rounds are in flight, forms a round from the
+ *     admitted requests in submission order and runs it through the batched
+ *     engine (sj_engine_round: one graph replay per layer, however many
+ *     requests), so that requests arriving while a round runs join the next
+ *     one (SJ_SERVE_BATCHED).  A request of at least
+ *     small = min(10^6, round_points / 4) points forms a round of its own, and
+ *     a round of smaller ones stops before the next large one (and at
+ *     round_points points or max_requests requests), so that no small request
+ *     waits for a large one's work inside its round; a round of one request,
+ *     or of fewer than `small` points, runs as direct join calls, which cost
+ *     less than the graph sized for the largest round.  Or the server runs one
  *     join call per request in submission order (SJ_SERVE_PER_REQUEST, the
  *     baseline the batched form is measured against);
  *   - copies each round's results back on a second copy stream and marks its

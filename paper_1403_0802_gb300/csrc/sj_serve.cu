@@ -7,10 +7,11 @@
 //                 asynchronous host-to-device copy of their points (stream
 //                 copy_in; one event per admitted batch);
 //   rounds     -- with fewer than two rounds in flight, the admitted requests
-//                 (up to round_points / max_requests) form a round on stream
-//                 compute, which first waits for the copies it needs; the
-//                 round is one sj_engine_round (SJ_SERVE_BATCHED) or one join
-//                 call per request (SJ_SERVE_PER_REQUEST);
+//                 (up to round_points / max_requests; a large request alone,
+//                 small ones together) form a round on stream compute, which
+//                 first waits for the copies it needs; the round is one
+//                 sj_engine_round (SJ_SERVE_BATCHED) or one join call per
+//                 request (SJ_SERVE_PER_REQUEST);
 //   results    -- stream copy_out waits for the round and copies ids (and
 //                 distances) back; when its event completes, the round's
 //                 requests are done (completion time taken then) and their
@@ -268,10 +269,17 @@ bool sj_server::launch_round() {
     Round rd;
     rd.t_issue = now();
     int64_t tot = 0;
+    // Batched rounds merge consecutive small requests only: a request of at
+    // least `small` points forms a round of its own (a direct join, efficient
+    // alone), and a round of small requests stops before the next large one,
+    // so that no small request waits for a large one's work inside its round
+    // (in submission order, as in the per-request form).
+    const int64_t small = std::min<int64_t>(SMALL_ROUND, round_points / 4);
     while (!ready.empty()) {
         Req *q = ready.front();
         if (!rd.reqs.empty() && (m == SJ_SERVE_PER_REQUEST || tot + q->r.n > round_points ||
-                                 (int64_t)rd.reqs.size() >= max_requests))
+                                 (int64_t)rd.reqs.size() >= max_requests || q->r.n >= small ||
+                                 rd.reqs.front()->r.n >= small))
             break;
         ready.pop_front();
         rd.reqs.push_back(q);
@@ -295,7 +303,6 @@ bool sj_server::launch_round() {
     // (scans over every cell, grids for round_points) exceeds a few direct
     // launches when the round is small.
     sj_status st = SJ_OK;
-    const int64_t small = std::min<int64_t>(SMALL_ROUND, round_points / 4);
     if (m == SJ_SERVE_BATCHED && tot >= small && rd.reqs.size() > 1) {
         std::vector<sj_request> t(rd.reqs.size());
         for (size_t k = 0; k < rd.reqs.size(); ++k) {
