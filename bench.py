@@ -2,7 +2,7 @@
 
 Workloads (--workload):
   p2p    (default) P2P, 10,000,000 clustered points, 100,000 random-walk
-         polylines (2-40 vertices), window D = 100 m, grid 512 x 512
+         polylines (2-40 vertices), window D = 100 m, grid 448 x 448
   pip    PIP, 1,000,000 uniform points, 1,024 star polygons, grid 256 x 256
   pip3   PIP at scale, 100,000,000 clustered points against the 40,000-tile
          layer (--layer 1), the 14,000-tile heavy-tail layer (--layer 2) or the

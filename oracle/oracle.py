@@ -31,20 +31,41 @@ class Grid(C.Structure):
                 ("nx", C.c_int32), ("ny", C.c_int32)]
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP when available)."""
+_SO_SAN = os.path.join(_OUT_DIR, "libsj_oracle_san.so")
+
+
+def build(force: bool = False, sanitize: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP when available).  sanitize=True:
+    a separate build with AddressSanitizer and UndefinedBehaviorSanitizer
+    (single-threaded; a process loading it needs the ASan runtime preloaded)."""
     os.makedirs(_OUT_DIR, exist_ok=True)
-    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
-        return _SO
+    so = _SO_SAN if sanitize else _SO
+    if not force and os.path.exists(so) and os.path.getmtime(so) >= os.path.getmtime(_SRC):
+        return so
     base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11",
             "-Wall", "-Wno-unknown-pragmas"]
-    tmp = _SO + f".tmp{os.getpid()}"
+    tmp = so + f".tmp{os.getpid()}"
+    if sanitize:
+        subprocess.run(base + ["-g", "-fno-omit-frame-pointer", "-fsanitize=address,undefined",
+                               "-fno-sanitize-recover=undefined", _SRC, "-o", tmp, "-lm"], check=True)
+        os.replace(tmp, so)
+        return so
     try:
         subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
     except subprocess.CalledProcessError:
         subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True)
-    os.replace(tmp, _SO)
-    return _SO
+    os.replace(tmp, so)
+    return so
+
+
+def use(path: str):
+    """Load the oracle from `path` (e.g. the sanitized build) instead of the
+    default build; only before the first call."""
+    global _SO
+    with _lock:
+        if _lib is not None:
+            raise RuntimeError("the oracle is already loaded")
+        _SO = path
 
 
 def _load():
@@ -52,7 +73,7 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        lib = C.CDLL(build())
+        lib = C.CDLL(_SO if os.path.basename(_SO) != "libsj_oracle.so" else build())
         d, i32, i64, p = C.c_double, C.c_int32, C.c_int64, C.c_void_p
         gp = C.POINTER(Grid)
         sig = {

@@ -340,10 +340,11 @@ def pip_stars(n_points: int = 1_000_000, seed: int = SEED_BASE + 1, n_side: int 
 
 
 def p2p_walks(n_points: int = 10_000_000, n_lines: int = 100_000, seed: int = SEED_BASE + 2,
-              D: float = 100.0, grid_n: int = 512, shard: int = 0) -> Workload:
+              D: float = 100.0, grid_n: int = 448, shard: int = 0) -> Workload:
     """P2P, plain FP64 method: mixture points against random-walk polylines with
-    2-40 vertices, window D = 100 m, filter grid 512 x 512 (the fastest of
-    256..2048 per axis on GB300 with per-cell segment lists)."""
+    2-40 vertices, window D = 100 m, filter grid 448 x 448 (the fastest of
+    384..768 per axis on GB300 with the current kernels: 0.796 ms per join
+    against 0.820 at 512)."""
     rng = np.random.default_rng(seed)
     sizes = rng.integers(2, 41, size=n_lines)
     layer = random_walks(rng, sizes)
@@ -357,13 +358,14 @@ def pip_tiles(n_points: int = 100_000_000, layer: int = 1, seed: int = SEED_BASE
     """PIP at scale: clustered points against a disjoint tiling.  Layer 1: 200 x 200
     tiles, side counts lognormal(median 2.6, sigma 1) capped at 1,250, three giant
     tiles (polygon median ~19, max ~5,000).  Layer 2: 140 x 100 tiles, side median
-    90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000).  Filter
-    grid 1024 x 1024 (the fastest of 512 / 1024 / 2048 per axis for both layers
-    at 100 M points on GB300).  Layer 3 (multi-ring, WWF-like): layer 1's
-    tiling with island holes in 30 % of the tiles (with_islands), about 70,000
-    polygons."""
+    90, cap 25,000, three giant tiles (polygon median ~500, max ~100,000).  Layer 3
+    (multi-ring, WWF-like): layer 1's tiling with island holes in 30 % of the
+    tiles (with_islands), about 70,000 polygons.  Filter grid per layer: the
+    fastest of 768..1536 per axis at 100 M points on GB300 -- 1536 x 1536 for
+    layers 1 and 2 (layer 2: 5.3 ms per join against 6.5 at 1024), 1280 x 1280
+    for layer 3."""
     if grid_n is None:
-        grid_n = 1024
+        grid_n = {1: 1536, 2: 1536, 3: 1280}[layer]
     rng = np.random.default_rng(seed + 10 * layer)
     if layer == 1:
         P = tiling(rng, 200, 200, side_median=2.6, side_cap=1250, n_giant=3)
