@@ -86,6 +86,8 @@ def parse(argv=None):
     ap.add_argument("--grid", type=int, default=0, help="filter grid cells per axis (0: the workload's)")
     ap.add_argument("--ppi", type=int, default=0, help="points per work item, 1..128 (0: library default 128)")
     ap.add_argument("--requests", type=int, default=10000, help="serve: stream length")
+    ap.add_argument("--serve-grid-pip", type=int, default=1024, help="serve: grid cells per axis, polygon layer")
+    ap.add_argument("--serve-grid-p2p", type=int, default=512, help="serve: grid cells per axis, polyline layer")
     ap.add_argument("--no-baselines", action="store_true", help="skip the FP64, e2e and CPU comparison legs")
     ap.add_argument("--no-extra", action="store_true", help="default run: leave out the PIP and serving legs")
     ap.add_argument("--oracle-full", action="store_true",
@@ -693,7 +695,8 @@ def serve_leg_child(args):
     buffers, the oracle's host threads -- that slows a host-bound serving loop
     run after them in the same process."""
     cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--workload", "serve", "--requests", str(args.requests),
-           "--form", args.form]
+           "--form", args.form, "--serve-grid-pip", str(args.serve_grid_pip), "--serve-grid-p2p",
+           str(args.serve_grid_p2p)]
     r = subprocess.run(cmd, capture_output=True, text=True)
     lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
     if r.returncode != 0 or not lines:
@@ -710,8 +713,11 @@ def serve_leg(args):
     from paper_1403_0802_gb300 import api, build, serve, synth
     build.build()
     torch.cuda.set_device(local)
-    wp = synth.pip_tiles(n_points=20_000_000, layer=1)
-    wl = synth.p2p_walks_lognormal(n_points=20_000_000, n_lines=150_000, D=100.0)
+    # serving grids: every join pays for a scan over the grid's cells, which
+    # dominates requests of a few thousand points, so the serving layers use
+    # coarser grids than the 100 M-point joins
+    wp = synth.pip_tiles(n_points=20_000_000, layer=1, grid_n=args.serve_grid_pip)
+    wl = synth.p2p_walks_lognormal(n_points=20_000_000, n_lines=150_000, D=100.0, grid_n=args.serve_grid_p2p)
     pip = api.pip_layer(wp.polygons.verts, wp.polygons.ring_off, wp.polygons.poly_ring_off, wp.grid)
     p2p = api.p2p_layer(wl.polylines.verts, wl.polylines.line_off, wl.D, wl.grid)
     pool_p = torch.from_numpy(wp.points).pin_memory()
@@ -755,6 +761,7 @@ def serve_leg(args):
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.form == "fp32x" else "f64", "data": "synthetic",
             "config": {"workload": f"serve_{args.requests}req_pip40k_p2p150k", "requests": args.requests,
+                       "grids": f"PIP {args.serve_grid_pip}^2, P2P {args.serve_grid_p2p}^2",
                        "sizes": "log-uniform 1e3..5e6 points", "mix": "70% PIP / 30% P2P (D=100 m)",
                        "arrivals": "Poisson, rate = rho x capacity of the plain FP64 one-join-per-request form",
                        "form": args.form, "server": "native (sj_server_*), batched engine rounds",

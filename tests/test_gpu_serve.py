@@ -198,8 +198,8 @@ def test_serving_on_the_full_layers(oracle):
         pytest.skip("no CUDA device")
     from paper_1403_0802_gb300 import api, build, serve
     build.build()
-    wp = synth.pip_tiles(n_points=8_000_000, layer=1)
-    wl = synth.p2p_walks_lognormal(n_points=8_000_000, n_lines=150_000, D=100.0)
+    wp = synth.pip_tiles(n_points=8_000_000, layer=1, grid_n=1024)
+    wl = synth.p2p_walks_lognormal(n_points=8_000_000, n_lines=150_000, D=100.0, grid_n=512)
     P, L = wp.polygons, wl.polylines
     pref = PIPRef(oracle, wp.grid, P.verts, P.ring_off, P.poly_ring_off)
     lref = P2PRef(oracle, wl.grid, L.verts, L.line_off, wl.D)
