@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
         for (int q = lane; q < np; q += 32) {
             double2 p = make_double2(0.0, 0.0);
             if (SJ_IN_BOUNDS(j0 + q < a.npts && (a.spts || a.perm[j0 + q] < a.npts), BND_PIP_POINT))
-                p = slot_point(a, j0 + q);
+                p = slot_point_l2(a, j0 + q);
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
