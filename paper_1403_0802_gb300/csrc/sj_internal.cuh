@@ -317,12 +317,6 @@ struct RefineArgs {
 __device__ __forceinline__ double2 slot_point(const RefineArgs &a, int j) {
     return a.spts ? a.spts[j] : a.pts[a.perm[j]];
 }
-// The same, read through L2 only (no L1 allocation): for the one read of each
-// point per work item, which would otherwise evict the edge and segment
-// records that items of one cell share in L1.
-__device__ __forceinline__ double2 slot_point_l2(const RefineArgs &a, int j) {
-    return a.spts ? __ldcg(a.spts + j) : __ldcg(a.pts + a.perm[j]);
-}
 
 // Order key of a y-value with -0 folded onto +0 (IEEE compares treat them as
 // equal; the order key alone would not).

@@ -252,6 +252,8 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
     // item), else in a fixed stride.
     // a.claim consecutive items per counter update (mostly chunks of one
     // cell, whose staged records are then still in L1).
+    // The next item's record and its cell's point range are loaded while the
+    // current item is refined, off the per-item chain of dependent loads.
     const int claim = a.claim > 1 ? a.claim : 1;
     int it = blockIdx.x * NW + w, it_end = it + 1;
     if (a.work_next) {
@@ -259,6 +261,13 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
         if (lane == 0) t0 = atomicAdd(a.work_next, claim);
         it = __shfl_sync(FULL, t0, 0);
         it_end = it + claim;
+    }
+    int2 item = make_int2(0, 0);
+    int cs0 = 0, cs1 = 0;
+    if (it < n_items) {
+        item = a.items[it];
+        cs0 = a.cell_start[item.x];
+        cs1 = a.cell_start[item.x + 1];
     }
     while (it < n_items) {
         int it_next = it + gridDim.x * NW;
@@ -268,26 +277,27 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
             else if (lane == 0) it_next = atomicAdd(a.work_next, claim);
         }
         ++c_items;
-        const int2 item = a.items[it];
         const int c = item.x;
-        const int j0 = a.cell_start[c] + item.y;
-        const int np = min(cell_chunk(a.ch, a.budget > 0 ? a.cell_work[c] : 0, a.budget), a.cell_start[c + 1] - j0);
+        const int j0 = cs0 + item.y;
+        const int np = min(cell_chunk(a.ch, a.budget > 0 ? a.cell_work[c] : 0, a.budget), cs1 - j0);
         const int k0 = a.cand_start[c], k1 = a.cand_start[c + 1];
         const float2 fo = cell_frame(a.frame_x, a.frame_y, a.g.nx, c);
 
-        // 1. points, the range of their FP32 y truncations and the smallest x truncation
+        // 1. points, the range of their FP32 y truncations and the smallest x
+        // truncation.  Items of more than 32 points: the (up to MAX_CH / 32)
+        // point loads of a lane are issued together -- every slot index, then
+        // every point as an asynchronous copy into the idle staging area -- so
+        // that their latencies overlap instead of forming one chain per point;
+        // smaller items (one point per lane) load directly.
         float ylo = FINF, yhi = -FINF, xlo = FINF;
-        for (int q = lane; q < np; q += 32) {
-            double2 p = make_double2(0.0, 0.0);
-            if (SJ_IN_BOUNDS(j0 + q < a.npts && (a.spts || a.perm[j0 + q] < a.npts), BND_PIP_POINT))
-                p = slot_point_l2(a, j0 + q);
+        auto put = [&](int q, double2 p, int src) {
             float hx, lx, hy, ly;
             split_double(p.x, hx, lx);
             split_double(p.y, hy, ly);
             if constexpr (FP32) {
                 s.pt[q] = make_float2(rel_coord(hx, lx, fo.x), rel_coord(hy, ly, fo.y));
                 s.pyh[q] = hy;
-                s.pin[q] = a.spts ? j0 + q : a.perm[j0 + q];
+                s.pin[q] = src;
             } else {
                 s.pt[q] = p;
             }
@@ -296,7 +306,50 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
             ylo = fminf(ylo, hy);
             yhi = fmaxf(yhi, hy);
             xlo = fminf(xlo, hx);
+        };
+        if (np <= 32) {
+            if (lane < np) {
+                int src = -1;
+                double2 p = make_double2(0.0, 0.0);
+                if (SJ_IN_BOUNDS(j0 + lane < a.npts, BND_PIP_POINT)) {
+                    src = a.spts ? j0 + lane : a.perm[j0 + lane];
+                    if (SJ_IN_BOUNDS(src < a.npts, BND_PIP_POINT)) p = a.spts ? __ldcg(a.spts + src) : __ldcg(a.pts + src);
+                    else src = -1;
+                }
+                put(lane, p, src);
+            }
+        } else {
+            constexpr int PQ = MAX_CH / 32;
+            double2 *pbuf;
+            if constexpr (FP32) {
+                static_assert(sizeof(PipSmem<true>::rel) >= MAX_CH * sizeof(double2), "");
+                pbuf = reinterpret_cast<double2 *>(&s.rel[0]);
+            } else {
+                static_assert(sizeof(PipSmem<false>::e) >= MAX_CH * sizeof(double2), "");
+                pbuf = reinterpret_cast<double2 *>(&s.e[0]);
+            }
+            __syncwarp();   // no lane still reads the previous item's staged edges
+            int src[PQ];
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                src[u] = (q < np && SJ_IN_BOUNDS(j0 + q < a.npts, BND_PIP_POINT)) ? (a.spts ? j0 + q : a.perm[j0 + q])
+                                                                                 : -1;
+                if (src[u] >= 0 && !SJ_IN_BOUNDS(src[u] < a.npts, BND_PIP_POINT)) src[u] = -1;
+            }
+#pragma unroll
+            for (int u = 0; u < PQ; ++u)
+                if (src[u] >= 0) copy16_async(pbuf + lane + 32 * u, a.spts ? a.spts + src[u] : a.pts + src[u]);
+            copy_async_wait_all();
+#pragma unroll
+            for (int u = 0; u < PQ; ++u) {
+                const int q = lane + 32 * u;
+                if (q < np) put(q, src[u] >= 0 ? pbuf[q] : make_double2(0.0, 0.0), src[u]);
+            }
         }
+        if (a.work_next) it_next = __shfl_sync(FULL, it_next, 0);
+        int2 item_n = make_int2(0, 0);
+        if (it_next < n_items) item_n = a.items[it_next];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             ylo = fminf(ylo, __shfl_xor_sync(FULL, ylo, o));
@@ -457,6 +510,11 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
             }
             __syncwarp();
         }
+        int cs0n = 0, cs1n = 0;
+        if (it_next < n_items) {
+            cs0n = a.cell_start[item_n.x];
+            cs1n = a.cell_start[item_n.x + 1];
+        }
         for (int q = lane; q < np; q += 32) {
             const int f = s.found[q];
             if (!SJ_IN_BOUNDS(j0 + q < a.npts, BND_PIP_RES)) continue;
@@ -465,9 +523,11 @@ __global__ void __launch_bounds__(NW * 32, 28 / NW) k_pip_refine(RefineArgs a) {
             if (f >= 0) ++c_hits;
         }
         __syncwarp();
-        it_next = a.work_next ? __shfl_sync(FULL, it_next, 0) : it_next;
         it_end = in_claim ? it_end : it_next + (a.work_next ? claim : 1);
         it = it_next;
+        item = item_n;
+        cs0 = cs0n;
+        cs1 = cs1n;
     }
     if (a.stats) {
         c_fb = __reduce_add_sync(FULL, c_fb);
