@@ -646,6 +646,10 @@ def run_ours(args):
     extra = {}
     if rank == 0 and world == 1 and args.workload == "p2p" and not args.no_extra and not args.points:
         import copy
+        # serving first: its host-bound loop measured the same on a fresh box
+        # whatever ran before, but its tail latencies grew 3-10x (both modes)
+        # minutes into a call on this shared machine
+        extra["serve"] = serve_leg_child(args)
         a1 = copy.copy(args)
         a1.workload, a1.ppi = "pip", 0
         ws = workload(a1)
@@ -669,7 +673,6 @@ def run_ours(args):
             extra[f"p2p_at_scale_D{int(D)}"] = join_leg(api, a4, w4, dev, stream, 1, sub_steps(15.0, args.steps), 3,
                                                         peaks, baselines=not args.no_baselines)
         del w4
-        extra["serve"] = serve_leg_child(args)
     if rank == 0:
         line = {
             "metric": metric_name(w.kind), "value": head["value"], "unit": "points/s", "n_gpus": world,
