@@ -469,7 +469,9 @@ def build_layer(api, w, dev, stream):
 
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-REFINE_SOURCES = {"p2p": ("paper_1403_0802_gb300/csrc/sj_p2p.cu",), "pip": ("paper_1403_0802_gb300/csrc/sj_pip.cu",)}
+# the sources a refine kernel is compiled from: its file and the shared header
+REFINE_SOURCES = {"p2p": ("paper_1403_0802_gb300/csrc/sj_p2p.cu", "paper_1403_0802_gb300/csrc/sj_internal.cuh"),
+                  "pip": ("paper_1403_0802_gb300/csrc/sj_pip.cu", "paper_1403_0802_gb300/csrc/sj_internal.cuh")}
 
 
 def sources_sha(kind):
@@ -483,7 +485,7 @@ def sources_sha(kind):
 def measured_traffic(kernel, workload, kind):
     """DRAM bytes (read + write) per launch of `kernel` on `workload` from the
     committed ncu summary profiles/traffic.txt (lines: kernel workload bytes
-    sha256-of-the-kernel's-source-file), or None when absent or when that file
+    sha256-of-the-kernel's-sources), or None when absent or when those sources
     changed since the counters were taken."""
     path = os.path.join(HERE, "profiles", "traffic.txt")
     if not os.path.exists(path):
