@@ -6,6 +6,7 @@
 //     and the per-cell candidate lists (the VPP relation) in CSR form.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 
 #include "sj_internal.cuh"
 
@@ -196,11 +197,15 @@ __global__ void k_cell_hist(BucketArgs a) {
     const int lS = a.sub_lx + a.sub_ly;
     const int sentinel = a.g.G << lS;
     unsigned resolved = 0, rhits = 0;
-    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
+    // A thread takes the pairs of points (2q, 2q + 1), q = q0, q0 + T, ...: the
+    // keys of a pair leave in one 16-byte store.
+    const unsigned pairs = ((unsigned)a.n + 1u) / 2u;
+    for (unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < pairs; q0 += (UNR / 2) * T) {
+        auto elem = [&](int u) { return 2u * (q0 + (unsigned)(u >> 1) * T) + (unsigned)(u & 1); };
         double2 p[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const unsigned i = i0 + u * T;
+            const unsigned i = elem(u);
             if (i < (unsigned)a.n) p[u] = a.pts[i];
         }
         // key (sentinel outside the grid), rank in its counter; a point of a
@@ -208,7 +213,7 @@ __global__ void k_cell_hist(BucketArgs a) {
         int c[UNR], r[UNR], v[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-            const unsigned i = i0 + u * T;
+            const unsigned i = elem(u);
             c[u] = sentinel;
             r[u] = 0;
             v[u] = CELL_REFINE;
@@ -225,10 +230,17 @@ __global__ void k_cell_hist(BucketArgs a) {
             }
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            const unsigned i = i0 + u * T;
-            if (i < (unsigned)a.n) {
+        for (int u = 0; u < UNR; u += 2) {
+            const unsigned i = elem(u);
+            if (i + 1u < (unsigned)a.n)
+                *reinterpret_cast<int4 *>(a.key_rank + i) = make_int4(c[u], r[u], c[u + 1], r[u + 1]);
+            else if (i < (unsigned)a.n)
                 a.key_rank[i] = make_int2(c[u], r[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const unsigned i = elem(u);
+            if (i < (unsigned)a.n) {
                 if (a.cell_res) {
                     if (v[u] != CELL_REFINE) {
                         a.out_id[i] = v[u];
@@ -307,16 +319,30 @@ struct BucketApply {
 
 __global__ void k_scatter(BucketArgs a) {
     const unsigned T = gridDim.x * blockDim.x;
-    for (unsigned i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < (unsigned)a.n; i0 += UNR * T) {
+    // pairs of points as in k_cell_hist: one 16-byte load of their keys, one
+    // 8-byte store of their slots
+    const unsigned pairs = ((unsigned)a.n + 1u) / 2u;
+    for (unsigned q0 = blockIdx.x * blockDim.x + threadIdx.x; q0 < pairs; q0 += (UNR / 2) * T) {
+        auto elem = [&](int u) { return 2u * (q0 + (unsigned)(u >> 1) * T) + (unsigned)(u & 1); };
         int2 k[UNR];
         double2 p[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-            const unsigned i = i0 + u * T;
-            k[u] = make_int2(a.g.G << (a.sub_lx + a.sub_ly), 0);
-            if (i < (unsigned)a.n) {
+        for (int u = 0; u < UNR; u += 2) {
+            const unsigned i = elem(u);
+            k[u] = k[u + 1] = make_int2(a.g.G << (a.sub_lx + a.sub_ly), 0);
+            if (i + 1u < (unsigned)a.n) {
+                const int4 kk = *reinterpret_cast<const int4 *>(a.key_rank + i);
+                k[u] = make_int2(kk.x, kk.y);
+                k[u + 1] = make_int2(kk.z, kk.w);
+            } else if (i < (unsigned)a.n) {
                 k[u] = a.key_rank[i];
-                if (a.spts) p[u] = a.pts[i];
+            }
+        }
+        if (a.spts) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const unsigned i = elem(u);
+                if (i < (unsigned)a.n) p[u] = a.pts[i];
             }
         }
         // With a.pos (cell_base set): only points of cells that yield work
@@ -338,15 +364,16 @@ __global__ void k_scatter(BucketArgs a) {
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             if (pos[u] >= 0 && SJ_IN_BOUNDS(pos[u] < a.n, BND_SCATTER)) {
-                a.perm[pos[u]] = (int)(i0 + u * T);
+                a.perm[pos[u]] = (int)elem(u);
                 if (a.spts) a.spts[pos[u]] = p[u];
             }
         }
         if (a.pos) {
 #pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const unsigned i = i0 + u * T;
-                if (i < (unsigned)a.n) a.pos[i] = pos[u];
+            for (int u = 0; u < UNR; u += 2) {
+                const unsigned i = elem(u);
+                if (i + 1u < (unsigned)a.n) *reinterpret_cast<int2 *>(a.pos + i) = make_int2(pos[u], pos[u + 1]);
+                else if (i < (unsigned)a.n) a.pos[i] = pos[u];
             }
         }
     }
@@ -374,6 +401,44 @@ __global__ void k_unsort(const int *pos, const int *res_id, const double *res_d,
             if (i < (unsigned)n && j[u] != POS_DONE) {
                 out_id[i] = id[u];
                 if (out_d) out_d[i] = d[u];
+            }
+        }
+    }
+}
+
+// Ids only, two consecutive points per thread and step (one 8-byte load of
+// their slots, one 8-byte store of their ids unless one of them was answered
+// by the cell-id pass); out_id 8-byte aligned.
+__global__ void k_unsort_ids2(const int *pos, const int *res_id, int n, int *out_id) {
+    const unsigned T = gridDim.x * blockDim.x;
+    const unsigned pairs = ((unsigned)n + 1u) / 2u;
+    for (unsigned p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < pairs; p0 += UNR * T) {
+        int2 j[UNR], id[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const unsigned p = p0 + u * T, i = 2u * p;
+            j[u] = make_int2(POS_DONE, POS_DONE);
+            if (p < pairs) {
+                if (i + 1u < (unsigned)n) j[u] = *reinterpret_cast<const int2 *>(pos + i);
+                else j[u].x = pos[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (j[u].x >= 0 && !SJ_IN_BOUNDS(j[u].x < n, BND_UNSORT)) j[u].x = -1;
+            if (j[u].y >= 0 && !SJ_IN_BOUNDS(j[u].y < n, BND_UNSORT)) j[u].y = -1;
+            id[u].x = j[u].x >= 0 ? res_id[j[u].x] : -1;
+            id[u].y = j[u].y >= 0 ? res_id[j[u].y] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const unsigned p = p0 + u * T, i = 2u * p;
+            if (p >= pairs) continue;
+            if (i + 1u < (unsigned)n && j[u].x != POS_DONE && j[u].y != POS_DONE) {
+                *reinterpret_cast<int2 *>(out_id + i) = id[u];
+            } else {
+                if (j[u].x != POS_DONE) out_id[i] = id[u].x;
+                if (i + 1u < (unsigned)n && j[u].y != POS_DONE) out_id[i + 1] = id[u].y;
             }
         }
     }
@@ -421,20 +486,80 @@ __global__ void k_unsort_rec(const int *pos, const R *res, int n, int *out_id, d
     }
 }
 
-cudaError_t launch_unsort_f(const int *pos, const ResF *res, int n, int *out_id, double *out_d, cudaStream_t s) {
-    const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
-    k_unsort_rec<ResF><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
+// The same with two consecutive points per thread and step: one 8-byte load of
+// their slots and 8- / 16-byte stores of their results, half the memory
+// instructions of the form above (whose load / store queue fills first).
+// out_id 8-byte and out_d 16-byte aligned.
+template <typename R>
+__global__ void k_unsort_rec2(const int *pos, const R *res, int n, int *out_id, double *out_d) {
+    const double inf = __longlong_as_double(0x7ff0000000000000LL);
+    const unsigned T = gridDim.x * blockDim.x;
+    const unsigned pairs = ((unsigned)n + 1u) / 2u;
+    for (unsigned p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < pairs; p0 += UNR * T) {
+        int2 j[UNR];
+        R r0[UNR], r1[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const unsigned p = p0 + u * T, i = 2u * p;
+            j[u] = make_int2(-1, -1);
+            if (p < pairs) {
+                if (i + 1u < (unsigned)n) j[u] = *reinterpret_cast<const int2 *>(pos + i);
+                else j[u].x = pos[i];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            if (j[u].x >= 0 && !SJ_IN_BOUNDS(j[u].x < n, BND_UNSORT)) j[u].x = -1;
+            if (j[u].y >= 0 && !SJ_IN_BOUNDS(j[u].y < n, BND_UNSORT)) j[u].y = -1;
+            if (j[u].x >= 0) r0[u] = res[j[u].x];
+            if (j[u].y >= 0) r1[u] = res[j[u].y];
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const unsigned p = p0 + u * T, i = 2u * p;
+            if (p >= pairs) continue;
+            const int id0 = j[u].x >= 0 ? r0[u].id : -1, id1 = j[u].y >= 0 ? r1[u].id : -1;
+            const double d0 = j[u].x >= 0 ? (double)r0[u].d : inf, d1 = j[u].y >= 0 ? (double)r1[u].d : inf;
+            if (i + 1u < (unsigned)n) {
+                *reinterpret_cast<int2 *>(out_id + i) = make_int2(id0, id1);
+                if (out_d) *reinterpret_cast<double2 *>(out_d + i) = make_double2(d0, d1);
+            } else {
+                out_id[i] = id0;
+                if (out_d) out_d[i] = d0;
+            }
+        }
+    }
+}
+
+template <typename R>
+static cudaError_t launch_unsort_rec(const int *pos, const R *res, int n, int *out_id, double *out_d,
+                                     cudaStream_t s) {
+    const bool paired = ((uintptr_t)out_id & 7) == 0 && ((uintptr_t)out_d & 15) == 0;
+    if (paired) {
+        const int nb = stream_blocks(((n + 1) / 2 + UNR - 1) / UNR, 256, 152 * 16);
+        k_unsort_rec2<R><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
+    } else {
+        const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
+        k_unsort_rec<R><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
+    }
     return cudaGetLastError();
 }
 
+cudaError_t launch_unsort_f(const int *pos, const ResF *res, int n, int *out_id, double *out_d, cudaStream_t s) {
+    return launch_unsort_rec(pos, res, n, out_id, out_d, s);
+}
+
 cudaError_t launch_unsort_d(const int *pos, const ResD *res, int n, int *out_id, double *out_d, cudaStream_t s) {
-    const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
-    k_unsort_rec<ResD><<<nb, 256, 0, s>>>(pos, res, n, out_id, out_d);
-    return cudaGetLastError();
+    return launch_unsort_rec(pos, res, n, out_id, out_d, s);
 }
 
 cudaError_t launch_unsort(const int *pos, const int *res_id, const double *res_d, int n, int *out_id, double *out_d,
                           cudaStream_t s) {
+    if (!res_d && !out_d && ((uintptr_t)out_id & 7) == 0) {
+        const int nb = stream_blocks(((n + 1) / 2 + UNR - 1) / UNR, 256, 152 * 16);
+        k_unsort_ids2<<<nb, 256, 0, s>>>(pos, res_id, n, out_id);
+        return cudaGetLastError();
+    }
     const int nb = stream_blocks((n + UNR - 1) / UNR, 256, 152 * 16);
     k_unsort<<<nb, 256, 0, s>>>(pos, res_id, res_d, n, out_id, out_d);
     return cudaGetLastError();
