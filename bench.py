@@ -117,7 +117,7 @@ def workload(args, rank: int = 0):
 # paper_1403_0802_gb300.autotune on GB300 (points per item x warps per block x
 # edges per chunk; 0 = the library default).
 TUNED = {"p2p": dict(ppi=128, block=4, edges=0), "pip": dict(ppi=128, block=4, edges=0),
-         "pip3_1": dict(ppi=128, block=8, edges=64), "pip3_2": dict(ppi=128, block=2, edges=64),
+         "pip3_1": dict(ppi=128, block=4, edges=64), "pip3_2": dict(ppi=128, block=2, edges=64),
          "pip3_3": dict(ppi=128, block=8, edges=64), "p2p4": dict(ppi=128, block=4, edges=0)}
 
 
