@@ -643,8 +643,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     baselines = rank == 0 and world == 1 and not args.no_baselines
     head = join_leg(api, args, w, dev, stream, world, args.steps, args.warmup, peaks, baselines=baselines)
-    # cell_hist, 3 scan phases, scatter; refine; FP32X P2P recheck; unsort
-    kernels_per_join = 5 + 1 + (1 if (w.kind == "p2p" and args.form == "fp32x") else 0) + 1
+    # cell_hist, the scan (2 phases up to 256 tiles of 1,024 cells, else 3), scatter; refine; FP32X P2P
+    # recheck; unsort
+    scan_tiles = (int(w.grid["nx"]) * int(w.grid["ny"]) + 1023) // 1024
+    kernels_per_join = 1 + (2 if scan_tiles <= 256 else 3) + 1 + 1 + (1 if (w.kind == "p2p" and args.form == "fp32x") else 0) + 1
     extra = {}
     if rank == 0 and world == 1 and args.workload == "p2p" and not args.no_extra and not args.points:
         import copy

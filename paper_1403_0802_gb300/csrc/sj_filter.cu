@@ -110,6 +110,43 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_apply(Load ld, Apply ap, int n,
     }
 }
 
+// Phases 2 and 3 in one launch for at most SCAN_FUSE tiles: each block sums
+// the (raw) sums of the tiles before it itself -- at most SCAN_FUSE - 1 loads
+// over the block -- and the last tile writes the grand totals.
+constexpr int SCAN_FUSE = 256;
+
+template <class Load, class Apply>
+__global__ void __launch_bounds__(SCAN_T) k_scan_apply_fused(Load ld, Apply ap, int n, int2 *block_sums, int nb,
+                                                             int *totals) {
+    int2 pre = make_int2(0, 0);
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += SCAN_T) pre = add2(pre, block_sums[k]);
+    int2 offset;
+    block_incl_scan<SCAN_T>(pre, offset);   // its total: the tile's exclusive prefix
+    int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_V;
+    int2 v[SCAN_V];
+    int2 tsum = make_int2(0, 0);
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+        int c = base + j;
+        v[j] = c < n ? ld(c) : make_int2(0, 0);
+        tsum = add2(tsum, v[j]);
+    }
+    int2 total;
+    int2 inc = block_incl_scan<SCAN_T>(tsum, total);
+    int2 ex = add2(sub2(inc, tsum), offset);
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+        int c = base + j;
+        if (c < n) ap(c, ex, v[j], n);
+        ex = add2(ex, v[j]);
+    }
+    if ((int)blockIdx.x == nb - 1 && threadIdx.x == 0) {
+        const int2 grand = add2(offset, total);
+        block_sums[nb] = grand;
+        if (totals) { totals[0] = grand.x; totals[1] = grand.y; }
+    }
+}
+
 // block_sums must hold at least nb + 1 entries (bucket_scan_blocks(n) does);
 // a smaller capacity is an error, not an out-of-bounds write.
 template <class Load, class Apply>
@@ -118,8 +155,12 @@ static cudaError_t run_scan(Load ld, Apply ap, int n, int2 *block_sums, size_t c
     if (nb == 0) nb = 1;
     if ((size_t)nb + 1 > cap) return cudaErrorInvalidValue;
     k_scan_reduce<Load><<<nb, SCAN_T, 0, s>>>(ld, n, block_sums);
-    k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, totals);
-    k_scan_apply<Load, Apply><<<nb, SCAN_T, 0, s>>>(ld, ap, n, block_sums);
+    if (nb <= SCAN_FUSE) {
+        k_scan_apply_fused<Load, Apply><<<nb, SCAN_T, 0, s>>>(ld, ap, n, block_sums, nb, totals);
+    } else {
+        k_scan_top<<<1, 1024, 0, s>>>(block_sums, nb, totals);
+        k_scan_apply<Load, Apply><<<nb, SCAN_T, 0, s>>>(ld, ap, n, block_sums);
+    }
     return cudaGetLastError();
 }
 
