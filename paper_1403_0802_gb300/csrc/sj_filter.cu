@@ -205,16 +205,19 @@ cudaError_t launch_thresholds(const GridDev &g, unsigned long long *kx, unsigned
 // ------------------------------------------------------------------ point bucketing
 
 // a1: cell id per point and per-cell count; the atomic's return value is the
-// point's rank inside its cell, so the scatter needs no second pass.  The
-// outputs are initialised here (-1 / +inf), refinement overwrites the hits.
-// Each thread handles UNR points per step (indices i, i + T, ..., T = total
-// threads) so that several independent load -> atomic -> store chains are in
-// flight at once.
+// point's rank inside its cell, so the scatter needs no second pass.  Points
+// whose result is known here (PIP whole-cell results, or the one-pass result
+// form's initial -1 / +inf) get their outputs written here.
+// Each thread handles UNR points per step so that several independent
+// load -> atomic -> store chains are in flight at once: UNR / 2 pairs of
+// consecutive points (2q, 2q + 1), q = q0, q0 + T, ... (T = total threads),
+// whose keys move as one 16-byte access (the scatter and the result gathers
+// take pairs the same way).
 constexpr int UNR = 4;
 
-// The step UNR * T can exceed the 2^22 headroom below 2^31 that the element
-// cap leaves, so the UNR kernels count in unsigned 32 bits: an index below
-// the cap plus a step below 2^31 stays below 2^32.
+// The step of the strided kernels can exceed the 2^22 headroom below 2^31
+// that the element cap leaves, so they count in unsigned 32 bits: an index
+// below the cap plus a step below 2^31 stays below 2^32.
 // Counter of a point: its cell, or with sub-cell order the cell's sub-cell
 // (from FP32 estimates of the position inside the cell: any deterministic
 // choice is a valid order); the sentinel G (G * S) outside the grid.
